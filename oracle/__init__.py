@@ -1,0 +1,8 @@
+"""CPU oracle (test infrastructure).
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+arm may import this package.  It wraps the plain C oracle in oracle.c with
+ctypes; nothing in it is shared with the CUDA path.
+"""
+from .oracle_lib import (OracleEnvs, OracleMachine, alu_adc, alu_sbc, base_cycles,  # noqa: F401
+                         build, philox4x32_10, preprocess, STATE_BYTES)

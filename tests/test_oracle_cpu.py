@@ -1,0 +1,334 @@
+"""Oracle pins for the 6507 core: checks against the arithmetic definition,
+the documented cycle rules and hand-computed program results."""
+import numpy as np
+import pytest
+
+from oracle import OracleMachine, alu_adc, alu_sbc, base_cycles
+from paper_1907_08467_gb300.synth.asm6502 import OPCODES
+from tests.helpers import JAM, rom, run_to_jam
+
+C, Z, D, V, N = 0x01, 0x02, 0x08, 0x40, 0x80
+
+
+def s8(v):
+    return v - 256 if v >= 128 else v
+
+
+def dec(v):
+    return 10 * (v >> 4) + (v & 15)
+
+
+def bcd(n):
+    return ((n // 10) << 4) | (n % 10)
+
+
+def test_adc_sbc_binary_exhaustive():
+    """All 256x256 operands x carry, binary mode, ADC and SBC, against the
+    two's-complement definition of the sum/difference and its flags."""
+    bad = []
+    for a in range(256):
+        for b in range(256):
+            for c in (0, 1):
+                r = alu_adc(a, b, c)
+                s = a + b + c
+                ss = s8(a) + s8(b) + c
+                exp_a = s % 256
+                exp_p = (C if s > 255 else 0) | (V if not -128 <= ss <= 127 else 0) | \
+                        (N if exp_a >= 128 else 0) | (Z if exp_a == 0 else 0)
+                if (r & 0xFF) != exp_a or ((r >> 8) & (C | Z | V | N)) != exp_p:
+                    bad.append(("adc", a, b, c))
+                r = alu_sbc(a, b, c)
+                d = a - b - (1 - c)
+                sd = s8(a) - s8(b) - (1 - c)
+                exp_a = d % 256
+                exp_p = (C if d >= 0 else 0) | (V if not -128 <= sd <= 127 else 0) | \
+                        (N if exp_a >= 128 else 0) | (Z if exp_a == 0 else 0)
+                if (r & 0xFF) != exp_a or ((r >> 8) & (C | Z | V | N)) != exp_p:
+                    bad.append(("sbc", a, b, c))
+    assert not bad, bad[:10]
+
+
+def test_adc_sbc_decimal_exhaustive():
+    """Decimal mode, all 256x256 operands x carry: valid-BCD operands against
+    decimal arithmetic mod 100; Z (ADC) and N, V, Z, C (SBC) against the
+    binary operation as on the NMOS part; invalid BCD is only required to
+    return a byte (its values follow the named NMOS description)."""
+    bad = []
+    for a in range(256):
+        for b in range(256):
+            valid = (a & 15) < 10 and (a >> 4) < 10 and (b & 15) < 10 and (b >> 4) < 10
+            for c in (0, 1):
+                r = alu_adc(a, b, c | D)
+                p = r >> 8
+                if ((p & Z) != 0) != (((a + b + c) & 0xFF) == 0):
+                    bad.append(("adcZ", a, b, c))
+                if valid:
+                    s = dec(a) + dec(b) + c
+                    if (r & 0xFF) != bcd(s % 100) or ((p & C) != 0) != (s >= 100):
+                        bad.append(("adc", a, b, c))
+                r = alu_sbc(a, b, c | D)
+                p = r >> 8
+                rb = alu_sbc(a, b, c)
+                if (p & (C | Z | V | N)) != ((rb >> 8) & (C | Z | V | N)):
+                    bad.append(("sbcflags", a, b, c))
+                if valid:
+                    d = dec(a) - dec(b) - (1 - c)
+                    if (r & 0xFF) != bcd(d % 100):
+                        bad.append(("sbc", a, b, c))
+                if p & D == 0:
+                    bad.append(("dflag", a, b, c))
+    assert not bad, bad[:10]
+
+
+def test_decimal_examples_from_description():
+    """Worked values of the NMOS decimal description (Clark, 6502.org):
+    99 + 1 = 00 carry set; 58 + 46 + 1 = 05 carry set; 12 + 34 = 46;
+    46 - 12 = 34; 40 - 13 = 27; 32 - 02 - 1 = 29; 12 - 21 = 91 borrow."""
+    assert alu_adc(0x99, 0x01, D) & 0x1FF == 0x100 | 0x00
+    assert alu_adc(0x58, 0x46, D | C) & 0x1FF == 0x100 | 0x05
+    assert alu_adc(0x12, 0x34, D) & 0x1FF == 0x46
+    assert alu_sbc(0x46, 0x12, D | C) & 0x1FF == 0x100 | 0x34
+    assert alu_sbc(0x40, 0x13, D | C) & 0x1FF == 0x100 | 0x27
+    assert alu_sbc(0x32, 0x02, D) & 0x1FF == 0x100 | 0x29
+    assert alu_sbc(0x12, 0x21, D | C) & 0x1FF == 0x91
+
+
+def test_documented_opcode_set():
+    """Exactly the 151 documented opcodes have a cycle count; the other 105 JAM."""
+    doc = {op for modes in OPCODES.values() for op in modes.values()}
+    assert len(doc) == 151
+    for op in range(256):
+        assert (base_cycles(op) > 0) == (op in doc), hex(op)
+
+
+# Documented timing rules per (class, addressing mode).
+READ = {"imm": 2, "zp": 3, "zpx": 4, "zpy": 4, "abs": 4, "abx": 4, "aby": 4, "izx": 6, "izy": 5}
+WRITE = {"zp": 3, "zpx": 4, "zpy": 4, "abs": 4, "abx": 5, "aby": 5, "izx": 6, "izy": 6}
+RMW = {"acc": 2, "zp": 5, "zpx": 6, "abs": 6, "abx": 7}
+OTHER = {"BRK": 7, "JSR": 6, "RTS": 6, "RTI": 6, "PHA": 3, "PHP": 3, "PLA": 4, "PLP": 4}
+
+
+def test_cycle_rules():
+    for mne, modes in OPCODES.items():
+        for mode, op in modes.items():
+            if mne in OTHER:
+                exp = OTHER[mne]
+            elif mne == "JMP":
+                exp = 3 if mode == "abs" else 5
+            elif mode == "rel":
+                exp = 2
+            elif mode == "imp":
+                exp = 2
+            elif mne in ("STA", "STX", "STY"):
+                exp = WRITE[mode]
+            elif mne in ("ASL", "LSR", "ROL", "ROR", "INC", "DEC"):
+                exp = RMW[mode]
+            else:
+                exp = READ[mode]
+            assert base_cycles(op) == exp, (mne, mode)
+
+
+def _cycles_of(src, setup="", n_setup=0):
+    """Cycles taken by the first instruction after `n_setup` setup instructions."""
+    m = OracleMachine(rom("Start:\n" + setup + src + "\n" + JAM))
+    for _ in range(n_setup):
+        m.step()
+    return m.step()
+
+
+def test_page_cross_and_branch_cycles():
+    assert _cycles_of("LDA $F0FF,X", "LDX #1\n", 1) == 5
+    assert _cycles_of("LDA $F0FE,X", "LDX #1\n", 1) == 4
+    assert _cycles_of("STA $80F0,X", "LDX #$20\n", 1) == 5
+    assert _cycles_of("LDA ($80),Y", "LDA #$FF\nSTA $80\nLDA #$F0\nSTA $81\nLDY #1\n", 5) == 6
+    assert _cycles_of("LDA ($80),Y", "LDA #$00\nSTA $80\nLDA #$F0\nSTA $81\nLDY #1\n", 5) == 5
+    # branch not taken / taken / taken across a page
+    assert _cycles_of("BNE Next\nNext:", "LDA #0\n", 1) == 2
+    assert _cycles_of("BEQ Next\nNext:", "LDA #0\n", 1) == 3
+    src = """
+Start:  LDA #0
+        JMP There
+        .org $F1FB
+There:  BEQ Far
+        .org $F208
+Far:    .byte $02
+"""
+    m = OracleMachine(rom(src))
+    m.step(); m.step()
+    assert m.step() == 4
+
+
+def test_arithmetic_loop_sum():
+    """Sum 1..10 with ADC in a loop: RAM $80 = 55 (hand computation)."""
+    m = OracleMachine(rom("""
+Start:  CLD
+        LDA #0
+        LDX #10
+Loop:   CLC
+        STX $81
+        ADC $81
+        DEX
+        BNE Loop
+        STA $80
+""" + JAM))
+    run_to_jam(m)
+    assert m.ram()[0] == 55
+
+
+def test_bcd_counter():
+    """Decimal counter incremented 150 times from 0: 0x50 with one carry out."""
+    m = OracleMachine(rom("""
+Start:  SED
+        LDA #0
+        STA $80
+        STA $81
+        LDX #150
+Loop:   LDA $80
+        CLC
+        ADC #1
+        STA $80
+        LDA $81
+        ADC #0
+        STA $81
+        DEX
+        BNE Loop
+        CLD
+""" + JAM))
+    run_to_jam(m)
+    assert m.ram()[0] == 0x50 and m.ram()[1] == 0x01
+
+
+def test_jsr_rts_stack_and_flags():
+    """Nested JSR/RTS, PHA/PLA, PHP pushes B and bit 5, PLP clears B."""
+    m = OracleMachine(rom("""
+Start:  LDX #$FF
+        TXS
+        JSR Sub1
+        STA $80
+        PHP
+        PLA
+        STA $81
+        LDA #$FF
+        PHA
+        PLP
+        PHP
+        PLA
+        STA $82
+        TSX
+        STX $83
+""" + JAM + """
+Sub1:   JSR Sub2
+        CLC
+        ADC #1
+        RTS
+Sub2:   LDA #$41
+        RTS
+"""))
+    run_to_jam(m)
+    ram = m.ram()
+    assert ram[0] == 0x42
+    assert ram[1] & 0x30 == 0x30          # B and bit 5 set in a pushed P
+    assert ram[2] == 0xFF                 # PLP of $FF then PHP: every bit set (B set again by PHP)
+    assert ram[3] == 0xFF                 # stack balanced
+    st = m.state()
+    assert st[0x04] & 0x10 == 0 and st[0x04] & 0x20 == 0x20  # live P: B clear, bit 5 set
+
+
+def test_jsr_pushes_last_byte_address():
+    m = OracleMachine(rom("""
+Start:  LDX #$FF
+        TXS
+Call:   JSR Sub
+""" + JAM + """
+Sub:    PLA
+        STA $80
+        PLA
+        STA $81
+""" + JAM))
+    run_to_jam(m)
+    # return address pushed = address of the JSR's last byte = Call + 2 = $F005
+    assert m.ram()[0] == 0x05 and m.ram()[1] == 0xF0
+
+
+def test_jmp_indirect_page_wrap():
+    """JMP ($F2FF) takes the low byte from $F2FF and the high byte from $F200."""
+    m = OracleMachine(rom("""
+Start:  JMP ($F2FF)
+        .org $F200
+        .byte $F4
+        .org $F2FF
+        .byte $00
+        .org $F300
+        .byte $F5
+        .org $F400
+        LDA #$AA
+        STA $80
+""" + JAM + """
+        .org $F500
+        LDA #$BB
+        STA $80
+""" + JAM))
+    run_to_jam(m)
+    assert m.ram()[0] == 0xAA
+
+
+def test_zero_page_index_wraps():
+    """zp,X and (zp,X) addressing.  On the 13-bit console bus the wrapped and
+    unwrapped page-0/page-1 addresses decode to the same RAM or TIA location,
+    so this checks that the accesses land there (TIA reads undriven bits 0)."""
+    m = OracleMachine(rom("""
+Start:  LDA #$5A
+        LDX #$90
+        STA $F0,X        ; ($F0+$90)&$FF = $80
+        LDA #$34
+        STA $FF
+        LDA #$12
+        STA $00          ; a TIA write (VSYNC)
+        LDA #$81
+        STA $FF
+        LDA #$00
+        LDX #$0F
+        LDA ($F0,X)      ; pointer at $FF,$00: low $81, high from $00 = TIA read (0)
+        STA $82
+""" + JAM))
+    run_to_jam(m)
+    ram = m.ram()
+    assert ram[0] == 0x5A
+    # pointer = $0081 -> RAM $81 (never written: 0)
+    assert ram[2] == 0x00
+
+
+def test_undocumented_opcode_jams():
+    m = OracleMachine(rom("Start: LDA #1\n STA $80\n .byte $02\n LDA #2\n STA $80\n"))
+    assert m.step() == 2
+    assert m.step() == 3
+    assert m.step() == -1
+    st = m.state()
+    assert st[0x1E] == 1 and m.ram()[0] == 1
+    assert m.step() == -1
+
+
+def test_power_on_state():
+    m = OracleMachine(rom("Start: NOP\n" + JAM))
+    st = m.state()
+    assert st[0] == st[1] == st[2] == 0
+    assert st[3] == 0xFD and st[4] == 0x24
+    assert int(st[6]) | int(st[7]) << 8 == 0xF000
+    assert not st[0x80:].any()
+    assert st[0x19] == 10  # timer interval 1024
+
+
+@pytest.mark.parametrize("op", ["ASL", "LSR", "ROL", "ROR"])
+def test_shifts_hand(op):
+    m = OracleMachine(rom(f"""
+Start:  SEC
+        LDA #$81
+        {op} A
+        STA $80
+        PHP
+        PLA
+        STA $81
+""" + JAM))
+    run_to_jam(m)
+    exp = {"ASL": (0x02, 1), "LSR": (0x40, 1), "ROL": (0x03, 1), "ROR": (0xC0, 1)}[op]
+    assert m.ram()[0] == exp[0] and (m.ram()[1] & 1) == exp[1]
