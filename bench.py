@@ -1,0 +1,343 @@
+"""Benchmark: raw emulated frames per second of the batched emulation path.
+
+One step = one pass of the whole path (interpreter for F frames with TIA
+logging, rasteriser, preprocessing, on-device reset) over every env of the
+workload.  Default workload: 4096 envs over 8 seeded 4 KB sprite cartridges,
+frame skip 4, 84x84x4 luma stack output, uniform random actions.
+
+Timing: W untimed warm-up steps, then K steps each timed on the device with
+CUDA events on the step's stream; L2 is flushed (a 256 MB write) before every
+timed step, outside the events.  value = envs * F * K / (sum of step times),
+max over ranks.  e2e = the same metric through the host-buffer entry point
+(actions copied in, observations, rewards and dones copied out every step).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--form plain|batched] [--config 2]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "raw emulated frames/sec on 1 GB300 vs plain GPU path and CPU oracle; p50/p99 step ms"
+SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
+
+# Warp instructions issued per env-frame by the interpreter kernel on the
+# default workload, from the ncu capture summarised in profiles/ (metric
+# sm__inst_executed.sum divided by the env-frames of the captured launch).
+# Refresh whenever the interpreter changes; None means not yet measured.
+INTERP_WARP_INST_PER_ENV_FRAME = {"plain": None, "batched": None}
+INTERP_DRAM_BYTES_PER_ENV_STEP = {"plain": None, "batched": None}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--form", default="plain", choices=["plain", "batched"])
+    p.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5])
+    p.add_argument("--n-envs", type=int, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def cpu_oracle_rate(w, seconds, seed=77, max_envs=512):
+    """The oracle timed on the host cores on a bounded sample of the workload:
+    the first `max_envs` envs (same cartridges, keys and actions), stepped
+    until `seconds` of wall time have passed."""
+    import numpy as np
+
+    from oracle import OracleEnvs
+    from paper_1907_08467_gb300 import synth
+    n = min(max_envs, w.n_envs)
+    idx = np.linspace(0, w.n_envs - 1, n).astype(np.int64)
+    cores = os.cpu_count() or 1
+    o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
+                   [w.env_rom[i] for i in idx], luma=synth.luma_table(), env_key=idx, seed=w.seed,
+                   sticky=w.sticky, output_mode=w.output_mode, frameskip=w.frameskip)
+    acts = synth.actions(seed, 4096, w.n_envs)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds and steps < 4096:
+        o.step(acts[steps][idx], n_threads=cores)
+        steps += 1
+    dt = time.perf_counter() - t0
+    frames = n * w.frameskip * steps
+    return {"value": frames / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {w.n_envs} envs (same cartridges, keys, actions) x {steps} steps, "
+                      f"{frames} frames in {dt:.1f} s on {cores} threads"}
+
+
+def reference_arm(args, w, ws, rank):
+    """The oracle as the reference arm: timed on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    sample_seconds = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    import numpy as np
+
+    from oracle import OracleEnvs
+    from paper_1907_08467_gb300 import synth
+    n = min(256, w.n_envs)
+    idx = np.linspace(0, w.n_envs - 1, n).astype(np.int64)
+    cores = os.cpu_count() or 1
+    o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
+                   [w.env_rom[i] for i in idx], luma=synth.luma_table(), env_key=idx, seed=w.seed,
+                   sticky=w.sticky, output_mode=w.output_mode, frameskip=w.frameskip)
+    acts = synth.actions(78, 100000, n)
+    s = 0
+    for _ in range(args.warmup):
+        o.step(acts[s], n_threads=cores)
+        s += 1
+    times, frames = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            o.step(acts[s], n_threads=cores)
+            s += 1
+            k += 1
+            if time.perf_counter() - t0 >= sample_seconds / 4 or k >= 64:
+                break
+        times.append(time.perf_counter() - t0)
+        frames += n * w.frameskip * k
+    total = sum(times)
+    val = frames / total
+    sample = f"{n} of {w.n_envs} envs x {s} steps on {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "n_envs": w.n_envs, "frameskip": w.frameskip, "sample_envs": n},
+        "cpu_baseline": {"value": val, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    from paper_1907_08467_gb300 import synth
+    w = synth.workload(args.config, n_envs=args.n_envs)
+    if args.impl == "reference":
+        reference_arm(args, w, ws, rank)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1907_08467_gb300.env import FORM_BATCHED, FORM_PLAIN, AtariEnv
+    torch.cuda.set_device(local)
+    form = FORM_BATCHED if args.form == "batched" else FORM_PLAIN
+    # replicas: each rank runs the whole workload with its own env keys
+    env_key = np.arange(w.n_envs, dtype=np.uint32) + np.uint32(rank * w.n_envs)
+    env = AtariEnv([r.data for r in w.roms], [(r.score_addr, r.gameover_addr) for r in w.roms], w.env_rom,
+                   luma=synth.luma_table(), env_key=env_key, frameskip=w.frameskip, sticky=w.sticky,
+                   output_mode=w.output_mode, form=form, seed=w.seed)
+    K, W = args.steps, args.warmup
+    acts = torch.from_numpy(synth.actions(100 + rank, K + W, w.n_envs)).cuda()
+    obs, rew, done = env.alloc_outputs()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for s in range(W):
+        env.step(acts[s], obs, rew, done)
+    torch.cuda.synchronize()
+    env.profile_read()
+    env.profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    instr = 0
+    logrec = 0
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for s in range(K):
+        flush.fill_(s & 0xFF)
+        ev[s][0].record(stream)
+        env.step(acts[W + s], obs, rew, done)
+        ev[s][1].record(stream)
+        a, b = env.counters()
+        instr += a
+        logrec += b
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    barrier(ws)
+    clk = clocks.stop()
+    env.profile(False)
+    prof = env.profile_read()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_s = sum(step_ms) / 1000.0
+    total_s_max = allreduce_max(total_s, ws)
+    frames = w.n_envs * w.frameskip * K
+    frames_all = allreduce_sum(frames, ws)
+    value = frames_all / total_s_max
+    ms_sorted = sorted(step_ms)
+    p50 = ms_sorted[len(ms_sorted) // 2]
+    p99 = ms_sorted[min(len(ms_sorted) - 1, int(round(0.99 * (len(ms_sorted) - 1))))]
+    gpu_launches = sum(v[1] for v in prof.values())
+
+    # e2e through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        ha = torch.from_numpy(synth.actions(200 + rank, 8 + K, w.n_envs)).pin_memory()
+        ho = torch.empty(env.obs_shape(), dtype=torch.uint8).pin_memory()
+        hr = torch.empty(w.n_envs, dtype=torch.int32).pin_memory()
+        hd = torch.empty(w.n_envs, dtype=torch.uint8).pin_memory()
+        for s in range(3):
+            env.step_host(ha[s], ho, hr, hd)
+        barrier(ws)
+        t0 = time.perf_counter()
+        for s in range(K):
+            env.step_host(ha[3 + s], ho, hr, hd)
+        dt = allreduce_max(time.perf_counter() - t0, ws)
+        e2e = {"value": frames_all / dt, "unit": "frames/s", "h2d_bytes_per_step": int(ha[0].numel()),
+               "d2h_bytes_per_step": int(ho.numel() + hr.numel() * 4 + hd.numel())}
+
+    # roofline of the dominant kernel (the interpreter): issue-slot use
+    interp_ms, interp_n = prof.get("interpreter", (0.0, 0))
+    roof = None
+    if interp_n:
+        dur = interp_ms / interp_n / 1000.0
+        per = INTERP_WARP_INST_PER_ENV_FRAME.get(args.form)
+        peak = SM_COUNT * SMSP_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+        ach = per * w.n_envs * w.frameskip / dur / 1e9 if per else None
+        tb = INTERP_DRAM_BYTES_PER_ENV_STEP.get(args.form)
+        roof = {"bound": "alu", "kernel": "interpreter", "achieved": ach, "peak": peak, "unit": "Gwarp-inst/s",
+                "frac": (ach / peak) if ach else None, "traffic": tb * w.n_envs if tb else None,
+                "launch_ms": dur * 1000.0, "share_of_step": interp_ms / max(1e-9, sum(step_ms)),
+                "m6502_inst_per_s": instr / total_s / 1e6 if instr else None,
+                "peak_source": "152 SMs x 4 schedulers x 2070 MHz (issue slots)"}
+    kernels = {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in prof.items()}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(w, args.cpu_seconds)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": 1000.0 * total_s_max / K, "p50_step_ms": p50, "p99_step_ms": p99,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded cartridges and actions)",
+            "config": {"workload": w.name, "n_envs": w.n_envs, "n_roms": len(w.roms), "frameskip": w.frameskip,
+                       "output": "84x84x4 uint8 stack" if w.output_mode == 1 else "210x160 palette frame",
+                       "form": args.form, "l2": "flushed (256 MB write) before each timed step",
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": e2e, "roofline": roof, "kernels": kernels, "gpu_launches": gpu_launches,
+            "m6502_inst_per_step": instr / K if K else None, "tia_log_records_per_step": logrec / K if K else None,
+            "wall_s": wall, "clocks": clk, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * atari_gpu.h -- C ABI of the batched Atari 2600 emulator for GB300 (sm_103a).
+ *
+ * The library steps thousands of independent consoles (MOS 6507 CPU, TIA
+ * video/collision chip, RIOT 6532 RAM/timer/ports, 2-16 KB cartridges with F8
+ * and F6 bank switching) in lockstep on one GPU.  It is the data-parallel
+ * emulation path of "Accelerating Reinforcement Learning through GPU Atari
+ * Emulation" (CuLE), Section 3: a CPU-interpreter kernel that logs TIA
+ * register writes to a per-env buffer in device memory, a TIA kernel that
+ * replays that buffer into 160x210 frames, only the last two frames of a
+ * four-frame skip rendered (their pixelwise maximum is the agent's input),
+ * and episode reset by copying one of 30 cached random start states.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 on success or a negative code (ATARI_E*).  Nothing throws
+ *     across the ABI.  atari_last_error() gives a thread-local message for
+ *     the last failing call on the calling thread.
+ *   - Pointers named d_* are DEVICE pointers on the device current when the
+ *     env was created; every other pointer is a host pointer.
+ *   - Device work is enqueued on the caller's stream (NULL = legacy default
+ *     stream).  atari_env_step does not synchronise the host.
+ *   - Per-env machine faults never fail a call: they set bits of the env's
+ *     status word (ATARI_ST_*), readable with atari_env_status.
+ *   - Ownership: the library owns all machine state, logs, frames, the start
+ *     state cache and its copies of the ROMs (ROM bytes are copied at create,
+ *     the caller may free them).  The caller owns action and output buffers.
+ */
+#ifndef ATARI_GPU_H
+#define ATARI_GPU_H
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ATARI_API __attribute__((visibility("default")))
+#else
+#define ATARI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct atari_env atari_env;   /* opaque, library-owned */
+typedef void *atari_stream;           /* a cudaStream_t */
+
+/* error codes */
+#define ATARI_OK 0
+#define ATARI_EINVAL (-22)   /* bad argument, ROM size or configuration */
+#define ATARI_ENOMEM (-12)   /* device or host allocation failed */
+#define ATARI_ECUDA (-5)     /* a CUDA runtime call failed (message has the CUDA error) */
+
+/* per-env status bits (sticky for the life of the env) */
+#define ATARI_ST_ILLEGAL 1u       /* undocumented opcode: CPU halted, env done at step end */
+#define ATARI_ST_FRAME_CAP 2u     /* a frame ran 400 lines without a VSYNC rise */
+#define ATARI_ST_LOG_OVERFLOW 4u  /* a rendered frame wrote more TIA registers than log_cap */
+#define ATARI_ST_BAD_ACTION 8u    /* an action >= 18 was taken as NOOP */
+
+/* output modes */
+#define ATARI_OUT_PALETTE 0  /* d_obs = uint8 [n][210][160] palette values (COLU & 0xFE) of frame F */
+#define ATARI_OUT_STACK 1    /* d_obs = uint8 [n][4][84][84] luma stack, slot 3 newest */
+
+/* execution forms */
+#define ATARI_FORM_PLAIN 0      /* one launch per kernel per step, state/RAM/ROM in global memory */
+#define ATARI_FORM_BATCHED 1    /* ROM-grouped persistent interpreter (RAM/ROM in shared memory),
+                                   fused rasterise+preprocess, whole step captured in a CUDA graph */
+
+/* RAM addresses ($80-$FF) of a cartridge's score byte (reward = per-frame
+ * int8 delta, summed over the step) and game-over byte (done when nonzero). */
+typedef struct {
+    uint8_t score_addr;
+    uint8_t gameover_addr;
+} atari_rom_meta;
+
+typedef struct {
+    int frameskip;        /* frames per step F, 2..16 (paper: 4); frames F-1 and F are rendered */
+    int sticky;           /* 1: each frame repeats the previous frame's action with p = 1/4 */
+    int n_cache;          /* cached start states per ROM, 1..64 (paper: 30) */
+    int startup_frames;   /* no-op frames from power-on before the first cached state (paper: 64) */
+    int max_noops;        /* extra random no-op frames, 0..max_noops (paper: up to 30) */
+    int output_mode;      /* ATARI_OUT_* */
+    int form;             /* ATARI_FORM_* */
+    int log_cap;          /* TIA-write log entries per rendered frame (>= 256; default 4096) */
+    int envs_per_block;   /* interpreter threads per block (batched form; 0 = autotune) */
+    uint64_t seed;        /* Philox4x32-10 key for start states, resets and sticky draws */
+} atari_config;
+
+/* Fill *cfg with the paper's defaults: F = 4, no sticky actions, 30 cached
+ * states, 64 start-up frames, up to 30 no-ops, stack output, batched form,
+ * log_cap 4096, autotuned block size, seed 1. */
+ATARI_API void atari_default_config(atari_config *cfg);
+
+/*
+ * Create n_envs environments.  roms[r] (host) holds rom_sizes[r] bytes:
+ * 2048 or 4096 (plain, 2K mirrored), 8192 (F8) or 16384 (F6); other sizes
+ * return ATARI_EINVAL.  env_rom[i] (host, n_envs) picks env i's cartridge;
+ * env_key[i] (host, may be NULL = i) keys env i's random streams, so a
+ * subset of envs created with the same keys reproduces the same run.
+ * luma (host, 128 bytes) maps palette index (value >> 1) to luma; required
+ * for ATARI_OUT_STACK, ignored otherwise.  Builds the start-state cache on
+ * the device (Section 3, reset strategy) and resets every env to
+ * cache[rom][mulhi32(philox(seed, env_key, 0, 2 << 8, 0), n_cache)].
+ * Synchronous.  On success *out receives the env.
+ */
+ATARI_API int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const atari_rom_meta *meta,
+                     int n_roms, const int32_t *env_rom, const uint32_t *env_key, int n_envs,
+                     const atari_config *cfg, const uint8_t *luma, atari_env **out);
+
+/*
+ * Force a reset of the envs whose d_mask byte is nonzero (d_mask NULL: all):
+ * episode += 1, state <- cached start state, frame stack zeroed.
+ */
+ATARI_API int atari_env_reset(atari_env *env, const uint8_t *d_mask, atari_stream stream);
+
+/*
+ * One step of every env: d_actions[i] (device, uint8, ALE action 0..17) is
+ * applied for F frames (sticky repeats drawn per frame when enabled).
+ * Writes d_obs (layout per output_mode), d_rewards[i] (int32: sum over the F
+ * frames of the int8 change of the score byte) and d_dones[i] (uint8: the
+ * game-over byte is nonzero after frame F, or the CPU halted).  Envs that are
+ * done are reset on the device after their observation is written; the
+ * observation returned is the terminal one.  Any output pointer may be NULL
+ * to skip that output.
+ */
+ATARI_API int atari_env_step(atari_env *env, const uint8_t *d_actions, uint8_t *d_obs, int32_t *d_rewards,
+                   uint8_t *d_dones, atari_stream stream);
+
+/*
+ * Same step with host buffers: copies actions host->device, steps, and
+ * copies obs / rewards / dones device->host on `stream`, then synchronises
+ * the stream.  Host pointers may be pageable or pinned; NULL skips.
+ */
+ATARI_API int atari_env_step_host(atari_env *env, const uint8_t *actions, uint8_t *obs, int32_t *rewards,
+                        uint8_t *dones, atari_stream stream);
+
+/* d_status (device, uint32 [n]) <- per-env status bits. */
+ATARI_API int atari_env_status(atari_env *env, uint32_t *d_status, atari_stream stream);
+
+/*
+ * Canonical per-env state, 256 bytes per env, little-endian (layout in the
+ * table below).  get copies n*256 bytes to d_dst; set loads them from d_src.
+ * A saved state restores a run exactly: the random streams are keyed by
+ * fields inside it.
+ *
+ *   0x00 A  0x01 X  0x02 Y  0x03 SP  0x04 P (bit 5 set, B clear)  0x05 bank
+ *   0x06 u16 PC   0x08 u64 CPU cycle   0x10 u64 RIOT timer write cycle
+ *   0x18 timer value  0x19 timer shift (0,3,6,10)  0x1A SWCHA out  0x1B SWACNT
+ *   0x1C SWCHB out  0x1D SWBCNT  0x1E jam  0x1F INPT4 latch
+ *   0x20..0x3F TIA: VSYNC VBLANK NUSIZ0 NUSIZ1 COLUP0 COLUP1 COLUPF COLUBK
+ *        CTRLPF REFP0 REFP1 PF0 PF1 PF2 ENAM0 ENAM1 ENABL(new) ENABL(old)
+ *        GRP0(new) GRP0(old) GRP1(new) GRP1(old) VDELP0 VDELP1 VDELBL
+ *        RESMP0 RESMP1 HMP0 HMP1 HMM0 HMM1 HMBL
+ *   0x40..0x44 positions P0 P1 M0 M1 BL (0..159)   0x46 u16 collision latches
+ *        (bit 2r+1 = D7, bit 2r = D6 of read register r)
+ *   0x48 u64 HMOVE-bar line (all ones: none)   0x50 u64 first line of frame
+ *   0x58 u32 frames since power-on
+ *   0x60 u32 episode  0x64 u32 step  0x68 u32 env key  0x6C u32 status
+ *   0x70 last applied action  0x71 score baseline  0x72 u16 ROM index
+ *   0x80..0xFF the 128 bytes of RAM
+ */
+ATARI_API int atari_env_get_state(atari_env *env, void *d_dst, atari_stream stream);
+ATARI_API int atari_env_set_state(atari_env *env, const void *d_src, atari_stream stream);
+
+/* d_dst <- the two rendered frames of the last step, uint8 [n][2][210][160]
+ * (frames F-1 and F, palette values).  Available in the plain form only
+ * (the batched form never materialises frames); ATARI_EINVAL otherwise. */
+ATARI_API int atari_env_get_frames(atari_env *env, uint8_t *d_dst, atari_stream stream);
+
+/* d_dst <- the start-state cache, [n_roms][n_cache][256] canonical states. */
+ATARI_API int atari_env_get_cache(atari_env *env, void *d_dst, atari_stream stream);
+
+/* Counters of the last step: 6502 instructions retired (sum over envs) and
+ * TIA log records written.  Host pointers; synchronises `stream`. */
+ATARI_API int atari_env_counters(atari_env *env, uint64_t *instructions, uint64_t *log_records, atari_stream stream);
+
+/*
+ * Per-kernel device timing.  With profiling enabled, every kernel launch of
+ * atari_env_step is bracketed by CUDA events recorded on the step's stream.
+ * atari_env_profile_read waits for the recorded work, then returns for each
+ * kernel slot the summed milliseconds and the launch count since the last
+ * read, and clears them.  ms and launches are host arrays of ATARI_PROF_SLOTS.
+ */
+#define ATARI_PROF_SLOTS 8
+#define ATARI_PROF_INTERP 0     /* 6507+RIOT interpreter (all frames of a step) */
+#define ATARI_PROF_RASTER 1     /* TIA replay into frames */
+#define ATARI_PROF_PREPROC 2    /* luma / max / 84x84 / stack */
+#define ATARI_PROF_FUSED 3      /* fused replay + preprocessing (batched form) */
+#define ATARI_PROF_COPY 4       /* output copies */
+ATARI_API int atari_env_profile(atari_env *env, int enable);
+ATARI_API int atari_env_profile_read(atari_env *env, double *ms, uint64_t *launches);
+
+/* Number of envs, and the bytes of device memory the env holds. */
+ATARI_API int atari_env_info(atari_env *env, int *n_envs, size_t *device_bytes);
+
+/* Device bytes atari_env_create would allocate for this configuration
+ * (used for admission against a memory budget). */
+ATARI_API size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg);
+
+/* Free everything; safe on NULL. */
+ATARI_API void atari_env_destroy(atari_env *env);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+ATARI_API const char *atari_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -40,7 +40,7 @@
  *   R11 power-on: registers and RAM 0, SP = 0xFD, P = 0x24, bank 0, PC from
  *       the reset vector, timer 0 with interval 1024 written at cycle 0.
  *   R12 undocumented opcodes halt the CPU (JAM, status ILLEGAL); the env is
- *       done at the end of that step.
+ *       done at the end of every step it ends halted, which also sets ILLEGAL.
  *   R13 decimal mode follows the NMOS behaviour described by B. Clark
  *       ("Decimal Mode", 6502.org): A and C by nibble adjustment, N and V
  *       from the intermediate result of ADC, Z (and all SBC flags) binary.
@@ -1087,6 +1087,7 @@ static void step_env(orc_envs *e, int i, uint8_t action, uint8_t *obs, int32_t *
         v->score_prev = s;
     }
     v->status |= v->m.status;
+    if (v->m.jam) v->status |= ORC_ST_ILLEGAL;   /* done because the CPU is halted */
     v->instret += v->m.instret - retired0;
     int d = v->m.ram[over_a] != 0 || v->m.jam;
     if (e->cfg.output_mode == 0) {

@@ -1,0 +1,874 @@
+// Batched Atari 2600 emulation on GB300 (sm_103a): kernels and the C ABI.
+//
+// Paper, Section 3 (CuLE): an Atari CPU kernel (one thread per emulator) and
+// a TIA kernel (renders from the CPU kernel's buffer of TIA writes), frames
+// rendered only where the agent needs them, reset from a cache of start
+// states.  The step here is: interpreter (all F frames, logging the writes of
+// frames F-1 and F) -> rasteriser -> preprocessing (luma, max of the two
+// frames, exact 84x84 area resampling, 4-frame stack); finished episodes are
+// reset inside the interpreter's epilogue.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/atari_gpu.h"
+#include "device_machine.cuh"
+#include "render.cuh"
+
+using namespace atari;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e__ = (expr);                                                            \
+    if (e__ != cudaSuccess)                                                              \
+      return fail(ATARI_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e__));     \
+  } while (0)
+
+// ------------------------------------------------------------------ decode table
+// The documented NMOS 6502 opcode matrix (row = high nibble, column = low
+// nibble); empty cells are undocumented opcodes, which halt the CPU.
+const char *const OPMAP[256] = {
+    "BRK imp", "ORA izx", 0, 0, 0, "ORA zp", "ASL zp", 0, "PHP imp", "ORA imm", "ASL acc", 0, 0, "ORA abs", "ASL abs", 0,
+    "BPL rel", "ORA izy", 0, 0, 0, "ORA zpx", "ASL zpx", 0, "CLC imp", "ORA aby", 0, 0, 0, "ORA abx", "ASL abx", 0,
+    "JSR abs", "AND izx", 0, 0, "BIT zp", "AND zp", "ROL zp", 0, "PLP imp", "AND imm", "ROL acc", 0, "BIT abs", "AND abs", "ROL abs", 0,
+    "BMI rel", "AND izy", 0, 0, 0, "AND zpx", "ROL zpx", 0, "SEC imp", "AND aby", 0, 0, 0, "AND abx", "ROL abx", 0,
+    "RTI imp", "EOR izx", 0, 0, 0, "EOR zp", "LSR zp", 0, "PHA imp", "EOR imm", "LSR acc", 0, "JMP abs", "EOR abs", "LSR abs", 0,
+    "BVC rel", "EOR izy", 0, 0, 0, "EOR zpx", "LSR zpx", 0, "CLI imp", "EOR aby", 0, 0, 0, "EOR abx", "LSR abx", 0,
+    "RTS imp", "ADC izx", 0, 0, 0, "ADC zp", "ROR zp", 0, "PLA imp", "ADC imm", "ROR acc", 0, "JMP ind", "ADC abs", "ROR abs", 0,
+    "BVS rel", "ADC izy", 0, 0, 0, "ADC zpx", "ROR zpx", 0, "SEI imp", "ADC aby", 0, 0, 0, "ADC abx", "ROR abx", 0,
+    0, "STA izx", 0, 0, "STY zp", "STA zp", "STX zp", 0, "DEY imp", 0, "TXA imp", 0, "STY abs", "STA abs", "STX abs", 0,
+    "BCC rel", "STA izy", 0, 0, "STY zpx", "STA zpx", "STX zpy", 0, "TYA imp", "STA aby", "TXS imp", 0, 0, "STA abx", 0, 0,
+    "LDY imm", "LDA izx", "LDX imm", 0, "LDY zp", "LDA zp", "LDX zp", 0, "TAY imp", "LDA imm", "TAX imp", 0, "LDY abs", "LDA abs", "LDX abs", 0,
+    "BCS rel", "LDA izy", 0, 0, "LDY zpx", "LDA zpx", "LDX zpy", 0, "CLV imp", "LDA aby", "TSX imp", 0, "LDY abx", "LDA abx", "LDX aby", 0,
+    "CPY imm", "CMP izx", 0, 0, "CPY zp", "CMP zp", "DEC zp", 0, "INY imp", "CMP imm", "DEX imp", 0, "CPY abs", "CMP abs", "DEC abs", 0,
+    "BNE rel", "CMP izy", 0, 0, 0, "CMP zpx", "DEC zpx", 0, "CLD imp", "CMP aby", 0, 0, 0, "CMP abx", "DEC abx", 0,
+    "CPX imm", "SBC izx", 0, 0, "CPX zp", "SBC zp", "INC zp", 0, "INX imp", "SBC imm", "NOP imp", 0, "CPX abs", "SBC abs", "INC abs", 0,
+    "BEQ rel", "SBC izy", 0, 0, 0, "SBC zpx", "INC zpx", 0, "SED imp", "SBC aby", 0, 0, 0, "SBC abx", "INC abx", 0,
+};
+
+const char *const MNEMONICS[] = {"JAM", "ADC", "AND", "ASL", "BCC", "BCS", "BEQ", "BIT", "BMI", "BNE", "BPL",
+                                 "BRK", "BVC", "BVS", "CLC", "CLD", "CLI", "CLV", "CMP", "CPX", "CPY", "DEC",
+                                 "DEX", "DEY", "EOR", "INC", "INX", "INY", "JMP", "JSR", "LDA", "LDX", "LDY",
+                                 "LSR", "NOP", "ORA", "PHA", "PHP", "PLA", "PLP", "ROL", "ROR", "RTI", "RTS",
+                                 "SBC", "SEC", "SED", "SEI", "STA", "STX", "STY", "TAX", "TAY", "TSX", "TXA",
+                                 "TXS", "TYA"};
+const char *const MODES[] = {"imp", "acc", "imm", "zp", "zpx", "zpy", "abs", "abx", "aby", "ind", "izx", "izy", "rel"};
+
+// Cycle counts from the documented timing rules of each instruction class.
+uint32_t cycles_for(uint32_t op, uint32_t mode, bool &penalty) {
+  penalty = false;
+  switch (op) {
+    case O_BRK: return 7;
+    case O_JSR: case O_RTS: case O_RTI: return 6;
+    case O_PHA: case O_PHP: return 3;
+    case O_PLA: case O_PLP: return 4;
+    case O_JMP: return mode == ABS ? 3 : 5;
+    default: break;
+  }
+  if (mode == REL || mode == IMP) return 2;
+  if (op == O_STA || op == O_STX || op == O_STY) {
+    switch (mode) {
+      case ZP: return 3; case ZPX: case ZPY: case ABS: return 4;
+      case ABX: case ABY: return 5; default: return 6;  // izx, izy
+    }
+  }
+  if (op == O_ASL || op == O_LSR || op == O_ROL || op == O_ROR || op == O_INC || op == O_DEC) {
+    switch (mode) {
+      case ACC: return 2; case ZP: return 5; case ZPX: case ABS: return 6; default: return 7;  // abx
+    }
+  }
+  penalty = mode == ABX || mode == ABY || mode == IZY;
+  switch (mode) {
+    case IMM: return 2; case ZP: return 3; case ZPX: case ZPY: case ABS: case ABX: case ABY: return 4;
+    case IZX: return 6; default: return 5;  // izy
+  }
+}
+
+std::vector<uint32_t> build_decode_table() {
+  std::vector<uint32_t> t(256, 0u);
+  for (int o = 0; o < 256; ++o) {
+    if (!OPMAP[o]) continue;
+    char mn[4] = {OPMAP[o][0], OPMAP[o][1], OPMAP[o][2], 0};
+    const char *md = OPMAP[o] + 4;
+    uint32_t op = 0, mode = 0;
+    for (uint32_t i = 0; i < sizeof(MNEMONICS) / sizeof(*MNEMONICS); ++i)
+      if (!strcmp(MNEMONICS[i], mn)) op = i;
+    for (uint32_t i = 0; i < sizeof(MODES) / sizeof(*MODES); ++i)
+      if (!strcmp(MODES[i], md)) mode = i;
+    bool pen;
+    uint32_t cyc = cycles_for(op, mode, pen);
+    t[o] = op | mode << 8 | cyc << 12 | (pen ? 1u : 0u) << 15;
+  }
+  return t;
+}
+
+// ------------------------------------------------------------------ kernels
+constexpr int ROM_SLOT = 16384;  // bytes reserved per cartridge image on the device
+
+struct RomInfo {
+  uint32_t scheme, score, gameover;
+};
+
+__device__ __forceinline__ RomInfo rom_info(const uint32_t *info, uint32_t r) {
+  uint32_t v = info[r];
+  return RomInfo{v & 0xFF, (v >> 8) & 0x7F, (v >> 16) & 0x7F};
+}
+
+// Copy a cached start state into an env's canonical state and re-key the
+// env fields (Section 3, reset strategy: a finished emulator takes a randomly
+// chosen cached start state in place of its terminal state).
+__device__ void reset_from_cache(uint8_t *st, const uint8_t *cache, const uint32_t *info, uint32_t rom,
+                                 uint32_t n_cache, uint64_t seed, uint32_t env_key, uint32_t episode) {
+  uint32_t idx = scale32(philox_x0(seed, env_key, 0u, PURPOSE_RESET << 8, episode), n_cache);
+  const uint8_t *src = cache + ((size_t)rom * n_cache + idx) * 256;
+  const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+  uint4 *d4 = reinterpret_cast<uint4 *>(st);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d4[i] = s4[i];     // 0x00..0x5F
+#pragma unroll
+  for (int i = 8; i < 16; ++i) d4[i] = s4[i];    // 0x80..0xFF
+  RomInfo ri = rom_info(info, rom);
+  st[S::LAST_ACTION] = 0;
+  st[S::SCORE_PREV] = src[S::RAM + ri.score];
+  Console<GlobalMem>::st32(st + S::EPISODE, episode);
+}
+
+// One thread per ROM: from power-on, run the start-up frames, then keep a
+// snapshot after each of the next max_noops + 1 frames.
+__global__ void k_cache_run(uint8_t *work, uint8_t *snaps, const uint8_t *roms, const uint32_t *info,
+                            const uint32_t *dec_g, int n_roms, int startup, int max_noops) {
+  __shared__ uint32_t dec[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) dec[i] = dec_g[i];
+  __syncthreads();
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_roms) return;
+  uint8_t *st = work + (size_t)r * 256;
+  Console<GlobalMem> m;
+  m.mem.ram = st + S::RAM;
+  m.mem.rom = roms + (size_t)r * ROM_SLOT;
+  m.dec = dec;
+  m.log.rec = nullptr;
+  m.log.n = 0;
+  m.log.cap = 0;
+  m.load(st);
+  m.scheme = rom_info(info, r).scheme;
+  for (int f = 0; f < startup; ++f) {
+    m.apply_action(0);
+    m.run_frame();
+  }
+  for (int j = 0; j <= max_noops; ++j) {
+    m.store(st);
+    uint8_t *dst = snaps + ((size_t)r * (max_noops + 1) + j) * 256;
+    for (int b = 0; b < 256; ++b) dst[b] = st[b];
+    if (j < max_noops) {
+      m.apply_action(0);
+      m.run_frame();
+    }
+  }
+}
+
+__global__ void k_cache_pick(uint8_t *cache, const uint8_t *snaps, int n_roms, int n_cache, int max_noops,
+                             uint64_t seed) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_roms * n_cache) return;
+  int r = t / n_cache, k = t % n_cache;
+  uint32_t n = scale32(philox_x0(seed, (uint32_t)r, (uint32_t)k, PURPOSE_CACHE << 8, 0u), (uint32_t)max_noops + 1);
+  const uint4 *src = reinterpret_cast<const uint4 *>(snaps + ((size_t)r * (max_noops + 1) + n) * 256);
+  uint4 *dst = reinterpret_cast<uint4 *>(cache + (size_t)t * 256);
+  for (int i = 0; i < 16; ++i) dst[i] = src[i];
+}
+
+// Initial reset (episode 0, fresh env fields) or a forced reset of masked envs.
+__global__ void k_reset(uint8_t *state, const uint8_t *cache, const uint32_t *info, const int32_t *env_rom,
+                        const uint32_t *env_key, const uint8_t *mask, uint8_t *ring, uint8_t *head, int n,
+                        int n_cache, uint64_t seed, int initial) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (mask && !mask[i]) return;
+  uint8_t *st = state + (size_t)i * 256;
+  uint32_t rom = (uint32_t)env_rom[i];
+  uint32_t episode;
+  if (initial) {
+    for (int b = 0x60; b < 0x80; ++b) st[b] = 0;
+    Console<GlobalMem>::st32(st + S::ENV_KEY, env_key[i]);
+    st[S::ROM] = rom & 0xFF;
+    st[S::ROM + 1] = rom >> 8;
+    episode = 0;
+  } else {
+    episode = Console<GlobalMem>::ld32(st + S::EPISODE) + 1;
+  }
+  reset_from_cache(st, cache, info, rom, (uint32_t)n_cache, seed, Console<GlobalMem>::ld32(st + S::ENV_KEY), episode);
+  if (ring) {
+    uint4 z{0, 0, 0, 0};
+    uint4 *p = reinterpret_cast<uint4 *>(ring + (size_t)i * 4 * 7056);
+    for (int q = 0; q < 4 * 7056 / 16; ++q) p[q] = z;
+    head[i] = 0;
+  }
+}
+
+struct StepArgs {
+  uint8_t *state;
+  const uint8_t *cache;
+  const uint8_t *roms;
+  const uint32_t *info;
+  const uint32_t *dec;
+  const uint8_t *actions;
+  int32_t *rew_int;
+  uint8_t *done_int;
+  int32_t *rew_out;
+  uint8_t *done_out;
+  uint32_t *log;
+  uint8_t *snap;
+  uint32_t *meta;
+  uint32_t *counters;
+  int n, frameskip, sticky, n_cache, log_cap, first_slot;
+  uint64_t seed;
+};
+
+// The per-env step body shared by the interpreter kernels.
+template <class Mem>
+__device__ void step_env(Console<Mem> &m, uint8_t *st, int i, const StepArgs &a, RomInfo ri) {
+  uint32_t action = a.actions[i];
+  uint32_t env_status = Console<Mem>::ld32(st + S::STATUS);
+  if (action >= 18) { env_status |= ST_BAD_ACTION; action = 0; }
+  const uint32_t env_key = Console<Mem>::ld32(st + S::ENV_KEY);
+  const uint32_t step_no = Console<Mem>::ld32(st + S::STEP);
+  uint32_t episode = Console<Mem>::ld32(st + S::EPISODE);
+  uint32_t last = st[S::LAST_ACTION];
+  uint32_t score_prev = st[S::SCORE_PREV];
+  int32_t reward = 0;
+  uint32_t log_total = 0;
+  const int F = a.frameskip;
+  for (int f = 1; f <= F; ++f) {
+    uint32_t act = action;
+    if (a.sticky) {
+      uint32_t u = philox_x0(a.seed, env_key, step_no, (uint32_t)f | PURPOSE_STICKY << 8, episode);
+      if (u < 0x40000000u) act = last;
+    }
+    last = act;
+    m.apply_action(act);
+    const int slot = f - (F - 1);
+    const bool logging = slot >= a.first_slot;
+    if (logging) {
+      m.snapshot(a.snap + ((size_t)i * 2 + slot) * 64);
+      m.log.rec = a.log + ((size_t)i * 2 + slot) * a.log_cap;
+      m.log.n = 0;
+      m.log.cap = (uint32_t)a.log_cap;
+    } else {
+      m.log.rec = nullptr;
+    }
+    uint32_t lines = m.run_frame();
+    if (logging) {
+      uint32_t *mt = a.meta + ((size_t)i * 2 + slot) * 2;
+      mt[0] = m.log.n;
+      mt[1] = lines;
+      log_total += m.log.n;
+    }
+    uint32_t s = m.mem.ram_rd(ri.score);
+    reward += (int32_t)(int8_t)(uint8_t)(s - score_prev);
+    score_prev = s;
+  }
+  env_status |= m.status;
+  if (m.jam) env_status |= ST_ILLEGAL;  // done because the CPU is halted
+  const uint32_t done = (m.mem.ram_rd(ri.gameover) != 0 || m.jam) ? 1u : 0u;
+  a.rew_int[i] = reward;
+  a.done_int[i] = (uint8_t)done;
+  if (a.rew_out) a.rew_out[i] = reward;
+  if (a.done_out) a.done_out[i] = (uint8_t)done;
+  if (a.counters) {
+    a.counters[2 * i] = m.instret;
+    a.counters[2 * i + 1] = log_total;
+  }
+  Console<Mem>::st32(st + S::STATUS, env_status);
+  Console<Mem>::st32(st + S::STEP, step_no + 1);
+  if (done) {
+    reset_from_cache(st, a.cache, a.info, Console<Mem>::ld32(st + S::ROM) & 0xFFFF, (uint32_t)a.n_cache, a.seed,
+                     env_key, episode + 1);
+  } else {
+    st[S::LAST_ACTION] = (uint8_t)last;
+    st[S::SCORE_PREV] = (uint8_t)score_prev;
+  }
+}
+
+// Plain form: one thread per env, state, RAM and ROM in global memory.
+__global__ void __launch_bounds__(128) k_interp_plain(StepArgs a) {
+  __shared__ uint32_t dec[256];
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) dec[t] = a.dec[t];
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  uint8_t *st = a.state + (size_t)i * 256;
+  uint32_t rom = st[S::ROM] | (uint32_t)st[S::ROM + 1] << 8;
+  RomInfo ri = rom_info(a.info, rom);
+  Console<GlobalMem> m;
+  m.mem.ram = st + S::RAM;
+  m.mem.rom = a.roms + (size_t)rom * ROM_SLOT;
+  m.dec = dec;
+  m.load(st);
+  m.scheme = ri.scheme;
+  step_env(m, st, i, a, ri);
+  // machine part written before a possible reset overwrote it: store first
+  // when not done; reset_from_cache already wrote the whole machine part
+  if (!a.done_int[i]) m.store(st);
+}
+
+// Rasteriser: one warp per (env, slot) frame.
+__global__ void __launch_bounds__(128) k_raster(const uint32_t *log, const uint8_t *snap, const uint32_t *meta,
+                                                uint8_t *frames, int n, int first_slot, int log_cap) {
+  __shared__ __align__(16) uint8_t rows[4][160];
+  const int warp = threadIdx.x >> 5;
+  const int slots = 2 - first_slot;
+  const long long w = (long long)blockIdx.x * 4 + warp;
+  if (w >= (long long)n * slots) return;
+  const int i = (int)(w / slots), slot = first_slot + (int)(w % slots);
+  const size_t fs = (size_t)i * 2 + slot;
+  RenderRegs R;
+  R.load(snap + fs * 64);
+  const uint32_t *mt = meta + fs * 2;
+  uint32_t n_rec = mt[0] < (uint32_t)log_cap ? mt[0] : (uint32_t)log_cap;
+  render_frame_warp(R, log + fs * log_cap, n_rec, mt[1], rows[warp], frames + fs * (FRAME_H * FRAME_W));
+}
+
+// Preprocessing: one block per env.  Luma of both frames, pixelwise maximum,
+// exact integer area resampling to 84x84 (round half up), push into the
+// env's 4-plane ring and write the ordered stack (oldest first) to obs.
+__global__ void __launch_bounds__(256) k_preprocess(const uint8_t *frames, const uint8_t *luma_g, uint8_t *ring,
+                                                    uint8_t *head, const uint8_t *done, uint8_t *obs, int n) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint8_t *mx = sm;                    // 210*160 luma maximum
+  uint8_t *luma = sm + FRAME_H * FRAME_W;
+  uint8_t *plane = luma + 128;         // 84*84 new plane
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  for (int t = threadIdx.x; t < 128; t += blockDim.x) luma[t] = luma_g[t];
+  __syncthreads();
+  const uint4 *f3 = reinterpret_cast<const uint4 *>(frames + (size_t)i * 2 * FRAME_H * FRAME_W);
+  const uint4 *f4 = f3 + FRAME_H * FRAME_W / 16;
+  for (int q = threadIdx.x; q < FRAME_H * FRAME_W / 16; q += blockDim.x) {
+    uint4 a = f3[q], b = f4[q];
+    const uint8_t *pa = reinterpret_cast<const uint8_t *>(&a);
+    const uint8_t *pb = reinterpret_cast<const uint8_t *>(&b);
+    uint4 r;
+    uint8_t *pr = reinterpret_cast<uint8_t *>(&r);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      uint8_t la = luma[pa[k] >> 1], lb = luma[pb[k] >> 1];
+      pr[k] = la > lb ? la : lb;
+    }
+    reinterpret_cast<uint4 *>(mx)[q] = r;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 84 * 84; o += blockDim.x) {
+    uint32_t oi = o / 84, oj = o % 84;
+    uint32_t y0 = (5u * oi) >> 1;
+    uint32_t wy0 = (oi & 1) ? 42u : 84u, wy1 = 84u, wy2 = (oi & 1) ? 84u : 42u;
+    uint32_t x0, wx0, wx1, wx2;
+    col_weights(oj, x0, wx0, wx1, wx2);
+    uint32_t s = 0;
+    const uint8_t *r0 = mx + y0 * FRAME_W + x0;
+    uint32_t rs0 = wx0 * r0[0] + wx1 * r0[1] + (wx2 ? wx2 * r0[2] : 0u);
+    const uint8_t *r1 = r0 + FRAME_W;
+    uint32_t rs1 = wx0 * r1[0] + wx1 * r1[1] + (wx2 ? wx2 * r1[2] : 0u);
+    const uint8_t *r2 = r1 + FRAME_W;
+    uint32_t rs2 = wx0 * r2[0] + wx1 * r2[1] + (wx2 ? wx2 * r2[2] : 0u);
+    s = wy0 * rs0 + wy1 * rs1 + wy2 * rs2;
+    plane[o] = (uint8_t)((s + 16800u) / 33600u);
+  }
+  __syncthreads();
+  const uint32_t h = head[i];
+  uint8_t *rg = ring + (size_t)i * 4 * 7056;
+  uint8_t *ob = obs ? obs + (size_t)i * 4 * 7056 : nullptr;
+  const uint32_t *pl32 = reinterpret_cast<const uint32_t *>(plane);
+  // obs slots 0..2 are the ring's planes h, h+1, h+2 (oldest first) -- the
+  // plane at h is the oldest and is about to be overwritten by the new one
+  if (ob) {
+    for (int s = 0; s < 3; ++s) {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(rg + ((h + 1 + s) & 3) * 7056);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(ob + s * 7056);
+      for (int q = threadIdx.x; q < 7056 / 4; q += blockDim.x) dst[q] = src[q];
+    }
+    uint32_t *dst = reinterpret_cast<uint32_t *>(ob + 3 * 7056);
+    for (int q = threadIdx.x; q < 7056 / 4; q += blockDim.x) dst[q] = pl32[q];
+  }
+  __syncthreads();
+  if (done[i]) {
+    uint32_t *z = reinterpret_cast<uint32_t *>(rg);
+    for (int q = threadIdx.x; q < 4 * 7056 / 4; q += blockDim.x) z[q] = 0;
+    if (threadIdx.x == 0) head[i] = 0;
+  } else {
+    uint32_t *dst = reinterpret_cast<uint32_t *>(rg + h * 7056);
+    for (int q = threadIdx.x; q < 7056 / 4; q += blockDim.x) dst[q] = pl32[q];
+    if (threadIdx.x == 0) head[i] = (uint8_t)((h + 1) & 3);
+  }
+}
+
+__global__ void k_status(const uint8_t *state, uint32_t *out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = Console<GlobalMem>::ld32(state + (size_t)i * 256 + S::STATUS);
+}
+
+template <class T>
+int dalloc(T **p, size_t bytes, size_t &total) {
+  if (bytes == 0) { *p = nullptr; return 0; }
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) return fail(ATARI_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  total += bytes;
+  return 0;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ env object
+struct atari_env {
+  int device = 0;
+  int n = 0, n_roms = 0;
+  atari_config cfg{};
+  size_t bytes = 0;
+  uint8_t *d_roms = nullptr;
+  uint32_t *d_info = nullptr;
+  uint32_t *d_dec = nullptr;
+  int32_t *d_env_rom = nullptr;
+  uint32_t *d_env_key = nullptr;
+  uint8_t *d_state = nullptr;
+  uint8_t *d_cache = nullptr;
+  uint32_t *d_log = nullptr;
+  uint8_t *d_snap = nullptr;
+  uint32_t *d_meta = nullptr;
+  uint8_t *d_frames = nullptr;
+  uint8_t *d_ring = nullptr;
+  uint8_t *d_head = nullptr;
+  uint8_t *d_luma = nullptr;
+  int32_t *d_rew = nullptr;
+  uint8_t *d_done = nullptr;
+  uint32_t *d_ctr = nullptr;
+  uint8_t *d_act = nullptr;   // staging for atari_env_step_host
+  uint8_t *d_obs_tmp = nullptr;
+  // profiling: (slot, start, end) event triples of the launches since the last read
+  bool profiling = false;
+  struct Rec { int slot; cudaEvent_t a, b; };
+  std::vector<Rec> prof;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+int scheme_of(size_t sz) {
+  if (sz == 2048 || sz == 4096) return 0;
+  if (sz == 8192) return 1;
+  if (sz == 16384) return 2;
+  return -1;
+}
+
+size_t obs_bytes(const atari_config &c) { return c.output_mode == ATARI_OUT_PALETTE ? 210 * 160 : 4 * 7056; }
+
+int validate(const atari_config &c) {
+  if (c.frameskip < 2 || c.frameskip > 16) return fail(ATARI_EINVAL, "frameskip must be in 2..16");
+  if (c.n_cache < 1 || c.n_cache > 64) return fail(ATARI_EINVAL, "n_cache must be in 1..64");
+  if (c.startup_frames < 0 || c.startup_frames > 100000) return fail(ATARI_EINVAL, "bad startup_frames");
+  if (c.max_noops < 0 || c.max_noops > 1000) return fail(ATARI_EINVAL, "bad max_noops");
+  if (c.output_mode != ATARI_OUT_PALETTE && c.output_mode != ATARI_OUT_STACK)
+    return fail(ATARI_EINVAL, "bad output_mode");
+  if (c.form != ATARI_FORM_PLAIN && c.form != ATARI_FORM_BATCHED) return fail(ATARI_EINVAL, "bad form");
+  if (c.log_cap < 256 || c.log_cap > (1 << 20)) return fail(ATARI_EINVAL, "log_cap must be in 256..2^20");
+  if (c.sticky != 0 && c.sticky != 1) return fail(ATARI_EINVAL, "sticky must be 0 or 1");
+  return 0;
+}
+
+}  // namespace
+
+namespace {
+cudaEvent_t take_event(atari_env *E) {
+  if (!E->pool.empty()) {
+    cudaEvent_t e = E->pool.back();
+    E->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+// RAII bracket: records start/end events around one launch when profiling.
+struct ProfScope {
+  atari_env *E;
+  int slot;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(atari_env *E_, int slot_, cudaStream_t s_) : E(E_), slot(slot_), s(s_) {
+    if (E->profiling) {
+      a = take_event(E);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = take_event(E);
+      cudaEventRecord(b, s);
+      E->prof.push_back({slot, a, b});
+    }
+  }
+};
+}  // namespace
+
+extern "C" {
+
+void atari_default_config(atari_config *c) {
+  if (!c) return;
+  memset(c, 0, sizeof *c);
+  c->frameskip = 4;
+  c->sticky = 0;
+  c->n_cache = 30;
+  c->startup_frames = 64;
+  c->max_noops = 30;
+  c->output_mode = ATARI_OUT_STACK;
+  c->form = ATARI_FORM_PLAIN;
+  c->log_cap = 4096;
+  c->envs_per_block = 0;
+  c->seed = 1;
+}
+
+const char *atari_last_error(void) { return g_err.c_str(); }
+
+size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg) {
+  if (!cfg || n_envs < 0 || n_roms < 0) return 0;
+  size_t n = (size_t)n_envs;
+  size_t b = 0;
+  b += (size_t)n_roms * ROM_SLOT + (size_t)n_roms * 4 + 1024;
+  b += n * (4 + 4 + 256);                                 // env_rom, env_key, state
+  b += (size_t)n_roms * cfg->n_cache * 256;               // cache
+  b += n * 2 * (size_t)cfg->log_cap * 4;                  // log
+  b += n * 2 * 64 + n * 2 * 2 * 4;                        // snapshots, meta
+  b += n * 2 * 210 * 160;                                 // frames (plain form)
+  if (cfg->output_mode == ATARI_OUT_STACK) b += n * 4 * 7056 + n;
+  b += n * (4 + 1 + 8 + 1);                               // rewards, dones, counters, action staging
+  return b;
+}
+
+int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const atari_rom_meta *meta, int n_roms,
+                     const int32_t *env_rom, const uint32_t *env_key, int n_envs, const atari_config *cfg,
+                     const uint8_t *luma, atari_env **out) {
+  g_err.clear();
+  if (!out) return fail(ATARI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!roms || !rom_sizes || !meta || n_roms <= 0 || n_roms > 65535) return fail(ATARI_EINVAL, "bad ROM list");
+  if (n_envs < 0 || (n_envs > 0 && !env_rom)) return fail(ATARI_EINVAL, "bad env list");
+  if (!cfg) return fail(ATARI_EINVAL, "cfg is NULL");
+  if (int e = validate(*cfg)) return e;
+  if (cfg->output_mode == ATARI_OUT_STACK && !luma) return fail(ATARI_EINVAL, "luma table required for stack output");
+  for (int r = 0; r < n_roms; ++r) {
+    if (!roms[r] || scheme_of(rom_sizes[r]) < 0)
+      return fail(ATARI_EINVAL, "ROM " + std::to_string(r) + ": size must be 2048, 4096, 8192 or 16384");
+    if (meta[r].score_addr < 0x80 || meta[r].gameover_addr < 0x80)
+      return fail(ATARI_EINVAL, "ROM " + std::to_string(r) + ": score/game-over addresses must be in $80-$FF");
+  }
+  for (int i = 0; i < n_envs; ++i)
+    if (env_rom[i] < 0 || env_rom[i] >= n_roms) return fail(ATARI_EINVAL, "env_rom out of range");
+
+  atari_env *E = new atari_env();
+  E->n = n_envs;
+  E->n_roms = n_roms;
+  E->cfg = *cfg;
+  cudaGetDevice(&E->device);
+  auto bail = [&](int code) {
+    atari_env_destroy(E);
+    return code;
+  };
+  size_t &T = E->bytes;
+  const size_t n = (size_t)n_envs;
+  const atari_config &c = E->cfg;
+  int rc = 0;
+  if ((rc = dalloc(&E->d_roms, (size_t)n_roms * ROM_SLOT, T)) || (rc = dalloc(&E->d_info, (size_t)n_roms * 4, T)) ||
+      (rc = dalloc(&E->d_dec, 1024, T)) || (rc = dalloc(&E->d_env_rom, n * 4, T)) ||
+      (rc = dalloc(&E->d_env_key, n * 4, T)) || (rc = dalloc(&E->d_state, n * 256, T)) ||
+      (rc = dalloc(&E->d_cache, (size_t)n_roms * c.n_cache * 256, T)) ||
+      (rc = dalloc(&E->d_log, n * 2 * (size_t)c.log_cap * 4, T)) || (rc = dalloc(&E->d_snap, n * 2 * 64, T)) ||
+      (rc = dalloc(&E->d_meta, n * 2 * 2 * 4, T)) || (rc = dalloc(&E->d_frames, n * 2 * 210 * 160, T)) ||
+      (rc = dalloc(&E->d_rew, n * 4, T)) || (rc = dalloc(&E->d_done, n, T)) || (rc = dalloc(&E->d_ctr, n * 8, T)) ||
+      (rc = dalloc(&E->d_act, n, T)) || (rc = dalloc(&E->d_luma, 128, T)))
+    return bail(rc);
+  if (c.output_mode == ATARI_OUT_STACK) {
+    if ((rc = dalloc(&E->d_ring, n * 4 * 7056, T)) || (rc = dalloc(&E->d_head, n, T))) return bail(rc);
+  }
+
+  // cartridges: 2K images mirrored to 4K, each in a 16 KB slot
+  std::vector<uint8_t> img((size_t)n_roms * ROM_SLOT, 0);
+  std::vector<uint32_t> info(n_roms);
+  std::vector<uint8_t> power((size_t)n_roms * 256, 0);
+  for (int r = 0; r < n_roms; ++r) {
+    uint8_t *dst = img.data() + (size_t)r * ROM_SLOT;
+    if (rom_sizes[r] == 2048) {
+      memcpy(dst, roms[r], 2048);
+      memcpy(dst + 2048, roms[r], 2048);
+    } else {
+      memcpy(dst, roms[r], rom_sizes[r]);
+    }
+    info[r] = (uint32_t)scheme_of(rom_sizes[r]) | (uint32_t)(meta[r].score_addr & 0x7F) << 8 |
+              (uint32_t)(meta[r].gameover_addr & 0x7F) << 16;
+    // power-on state: registers and RAM zero, SP $FD, P $24, PC from the reset
+    // vector of bank 0, timer 0 with interval 1024 written at cycle 0
+    uint8_t *p = power.data() + (size_t)r * 256;
+    p[S::SP] = 0xFD;
+    p[S::P] = 0x24;
+    p[S::PC] = dst[0xFFC];
+    p[S::PC + 1] = dst[0xFFD];
+    p[S::TIM_SHIFT] = 10;
+    for (int b = 0; b < 8; ++b) p[S::BAR_LINE + b] = 0xFF;
+  }
+  std::vector<uint32_t> dec = build_decode_table();
+  std::vector<uint32_t> keys(n);
+  for (size_t i = 0; i < n; ++i) keys[i] = env_key ? env_key[i] : (uint32_t)i;
+
+  auto up = [&](void *d, const void *h, size_t b) -> int {
+    if (!b) return 0;
+    cudaError_t e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? 0 : fail(ATARI_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
+  };
+  if ((rc = up(E->d_roms, img.data(), img.size())) || (rc = up(E->d_info, info.data(), info.size() * 4)) ||
+      (rc = up(E->d_dec, dec.data(), 1024)) || (rc = up(E->d_env_rom, env_rom, n * 4)) ||
+      (rc = up(E->d_env_key, keys.data(), n * 4)))
+    return bail(rc);
+  if (luma && (rc = up(E->d_luma, luma, 128))) return bail(rc);
+
+  // start-state cache (Section 3): run each ROM from power-on on the device
+  uint8_t *d_work = nullptr, *d_snaps = nullptr;
+  size_t scratch = 0;
+  if ((rc = dalloc(&d_work, (size_t)n_roms * 256, scratch)) ||
+      (rc = dalloc(&d_snaps, (size_t)n_roms * (c.max_noops + 1) * 256, scratch))) {
+    cudaFree(d_work);
+    return bail(rc);
+  }
+  rc = up(d_work, power.data(), power.size());
+  if (!rc) {
+    k_cache_run<<<(n_roms + 31) / 32, 32>>>(d_work, d_snaps, E->d_roms, E->d_info, E->d_dec, n_roms,
+                                           c.startup_frames, c.max_noops);
+    int tot = n_roms * c.n_cache;
+    k_cache_pick<<<(tot + 127) / 128, 128>>>(E->d_cache, d_snaps, n_roms, c.n_cache, c.max_noops, c.seed);
+    if (n_envs > 0)
+      k_reset<<<(n_envs + 127) / 128, 128>>>(E->d_state, E->d_cache, E->d_info, E->d_env_rom, E->d_env_key, nullptr,
+                                             E->d_ring, E->d_head, n_envs, c.n_cache, c.seed, 1);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) rc = fail(ATARI_ECUDA, std::string("cache build: ") + cudaGetErrorString(e));
+  }
+  cudaFree(d_work);
+  cudaFree(d_snaps);
+  if (rc) return bail(rc);
+  if (c.output_mode == ATARI_OUT_STACK) {
+    static bool attr_set = false;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!attr_set) {
+      cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+      attr_set = true;
+    }
+  }
+  *out = E;
+  return 0;
+}
+
+void atari_env_destroy(atari_env *E) {
+  if (!E) return;
+  void *ptrs[] = {E->d_roms, E->d_info, E->d_dec, E->d_env_rom, E->d_env_key, E->d_state, E->d_cache, E->d_log,
+                  E->d_snap, E->d_meta, E->d_frames, E->d_ring, E->d_head, E->d_luma, E->d_rew, E->d_done,
+                  E->d_ctr, E->d_act, E->d_obs_tmp};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (auto &r : E->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : E->pool) cudaEventDestroy(e);
+  delete E;
+}
+
+int atari_env_reset(atari_env *E, const uint8_t *d_mask, atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_reset<<<(E->n + 127) / 128, 128, 0, s>>>(E->d_state, E->d_cache, E->d_info, E->d_env_rom, E->d_env_key, d_mask,
+                                             E->d_ring, E->d_head, E->n, E->cfg.n_cache, E->cfg.seed, 0);
+  CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int atari_env_step(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32_t *d_rewards, uint8_t *d_dones,
+                   atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->n == 0) return 0;
+  if (!d_actions) return fail(ATARI_EINVAL, "d_actions is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const atari_config &c = E->cfg;
+  StepArgs a;
+  a.state = E->d_state;
+  a.cache = E->d_cache;
+  a.roms = E->d_roms;
+  a.info = E->d_info;
+  a.dec = E->d_dec;
+  a.actions = d_actions;
+  a.rew_int = E->d_rew;
+  a.done_int = E->d_done;
+  a.rew_out = d_rewards;
+  a.done_out = d_dones;
+  a.log = E->d_log;
+  a.snap = E->d_snap;
+  a.meta = E->d_meta;
+  a.counters = E->d_ctr;
+  a.n = E->n;
+  a.frameskip = c.frameskip;
+  a.sticky = c.sticky;
+  a.n_cache = c.n_cache;
+  a.log_cap = c.log_cap;
+  a.first_slot = 0;
+  a.seed = c.seed;
+  {
+    ProfScope p(E, ATARI_PROF_INTERP, s);
+    k_interp_plain<<<(E->n + 127) / 128, 128, 0, s>>>(a);
+  }
+  CUDA_TRY(cudaGetLastError());
+  long long warps = (long long)E->n * 2;
+  {
+    ProfScope p(E, ATARI_PROF_RASTER, s);
+    k_raster<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(E->d_log, E->d_snap, E->d_meta, E->d_frames, E->n, 0,
+                                                          c.log_cap);
+  }
+  CUDA_TRY(cudaGetLastError());
+  if (c.output_mode == ATARI_OUT_STACK) {
+    size_t smem = 210 * 160 + 128 + 7056;
+    {
+      ProfScope p(E, ATARI_PROF_PREPROC, s);
+      k_preprocess<<<E->n, 256, smem, s>>>(E->d_frames, E->d_luma, E->d_ring, E->d_head, E->d_done, d_obs, E->n);
+    }
+    CUDA_TRY(cudaGetLastError());
+  } else if (d_obs) {
+    ProfScope p(E, ATARI_PROF_COPY, s);
+    CUDA_TRY(cudaMemcpy2DAsync(d_obs, 210 * 160, E->d_frames + 210 * 160, 2 * 210 * 160, 210 * 160, E->n,
+                               cudaMemcpyDeviceToDevice, s));
+  }
+  return 0;
+}
+
+int atari_env_step_host(atari_env *E, const uint8_t *actions, uint8_t *obs, int32_t *rewards, uint8_t *dones,
+                        atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->n == 0) return 0;
+  if (!actions) return fail(ATARI_EINVAL, "actions is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ob = obs_bytes(E->cfg);
+  if (obs && !E->d_obs_tmp) {
+    size_t dummy = 0;
+    if (int rc = dalloc(&E->d_obs_tmp, (size_t)E->n * ob, dummy)) return rc;
+    E->bytes += dummy;
+  }
+  CUDA_TRY(cudaMemcpyAsync(E->d_act, actions, E->n, cudaMemcpyHostToDevice, s));
+  if (int rc = atari_env_step(E, E->d_act, obs ? E->d_obs_tmp : nullptr, nullptr, nullptr, stream)) return rc;
+  if (obs) CUDA_TRY(cudaMemcpyAsync(obs, E->d_obs_tmp, (size_t)E->n * ob, cudaMemcpyDeviceToHost, s));
+  if (rewards) CUDA_TRY(cudaMemcpyAsync(rewards, E->d_rew, (size_t)E->n * 4, cudaMemcpyDeviceToHost, s));
+  if (dones) CUDA_TRY(cudaMemcpyAsync(dones, E->d_done, (size_t)E->n, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return 0;
+}
+
+int atari_env_status(atari_env *E, uint32_t *d_status, atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->n == 0) return 0;
+  if (!d_status) return fail(ATARI_EINVAL, "d_status is NULL");
+  k_status<<<(E->n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(E->d_state, d_status, E->n);
+  CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int atari_env_get_state(atari_env *E, void *d_dst, atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->n == 0) return 0;
+  if (!d_dst) return fail(ATARI_EINVAL, "d_dst is NULL");
+  CUDA_TRY(cudaMemcpyAsync(d_dst, E->d_state, (size_t)E->n * 256, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return 0;
+}
+
+int atari_env_set_state(atari_env *E, const void *d_src, atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->n == 0) return 0;
+  if (!d_src) return fail(ATARI_EINVAL, "d_src is NULL");
+  CUDA_TRY(cudaMemcpyAsync(E->d_state, d_src, (size_t)E->n * 256, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return 0;
+}
+
+int atari_env_get_frames(atari_env *E, uint8_t *d_dst, atari_stream stream) {
+  g_err.clear();
+  if (!E || !d_dst) return fail(ATARI_EINVAL, "bad argument");
+  if (E->cfg.form != ATARI_FORM_PLAIN) return fail(ATARI_EINVAL, "frames are materialised by the plain form only");
+  CUDA_TRY(cudaMemcpyAsync(d_dst, E->d_frames, (size_t)E->n * 2 * 210 * 160, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+  return 0;
+}
+
+int atari_env_get_cache(atari_env *E, void *d_dst, atari_stream stream) {
+  g_err.clear();
+  if (!E || !d_dst) return fail(ATARI_EINVAL, "bad argument");
+  CUDA_TRY(cudaMemcpyAsync(d_dst, E->d_cache, (size_t)E->n_roms * E->cfg.n_cache * 256, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+  return 0;
+}
+
+int atari_env_counters(atari_env *E, uint64_t *instructions, uint64_t *log_records, atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  std::vector<uint32_t> h((size_t)E->n * 2);
+  if (E->n) {
+    CUDA_TRY(cudaMemcpyAsync(h.data(), E->d_ctr, h.size() * 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  }
+  uint64_t a = 0, b = 0;
+  for (int i = 0; i < E->n; ++i) { a += h[2 * i]; b += h[2 * i + 1]; }
+  if (instructions) *instructions = a;
+  if (log_records) *log_records = b;
+  return 0;
+}
+
+int atari_env_profile(atari_env *E, int enable) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  E->profiling = enable != 0;
+  return 0;
+}
+
+int atari_env_profile_read(atari_env *E, double *ms, uint64_t *launches) {
+  g_err.clear();
+  if (!E || !ms || !launches) return fail(ATARI_EINVAL, "bad argument");
+  for (int k = 0; k < ATARI_PROF_SLOTS; ++k) { ms[k] = 0; launches[k] = 0; }
+  for (auto &r : E->prof) {
+    CUDA_TRY(cudaEventSynchronize(r.b));
+    float t = 0;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.slot] += t;
+    launches[r.slot] += 1;
+    E->pool.push_back(r.a);
+    E->pool.push_back(r.b);
+  }
+  E->prof.clear();
+  return 0;
+}
+
+int atari_env_info(atari_env *E, int *n_envs, size_t *device_bytes) {
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (n_envs) *n_envs = E->n;
+  if (device_bytes) *device_bytes = E->bytes;
+  return 0;
+}
+
+}  // extern "C"

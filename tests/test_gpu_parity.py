@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element, bit-exact (integer and byte work: tolerance 0).
+
+Covers the start-state cache, every output of every step (observation,
+reward, done, the full 256-byte canonical state, both rendered frames), the
+four cartridge families (playfield, sprites/collisions, F8/F6 bank switching
+with sticky actions, random-program fuzz with halting opcodes), ragged and
+degenerate batch sizes, and the full 4096-env configuration on sampled envs.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import OracleEnvs
+from paper_1907_08467_gb300 import synth
+from paper_1907_08467_gb300.env import FORM_PLAIN, OUT_PALETTE, OUT_STACK, ST_BAD_ACTION, ST_LOG_OVERFLOW, AtariEnv
+
+pytestmark = pytest.mark.gpu
+
+STATE_FIELDS = [(0x00, "A"), (0x01, "X"), (0x02, "Y"), (0x03, "SP"), (0x04, "P"), (0x05, "bank"), (0x06, "PC"),
+                (0x08, "cycles"), (0x10, "timer_cw"), (0x18, "timer"), (0x1A, "ports"), (0x1E, "jam"),
+                (0x20, "TIA"), (0x40, "positions"), (0x46, "collisions"), (0x48, "bar"), (0x50, "frame_line"),
+                (0x58, "frame_no"), (0x60, "episode"), (0x64, "step"), (0x68, "env_key"), (0x6C, "status"),
+                (0x70, "last_action"), (0x71, "score_prev"), (0x72, "rom"), (0x80, "RAM")]
+
+
+def _field(off):
+    name = "?"
+    for o, n in STATE_FIELDS:
+        if o <= off:
+            name = n
+    return name
+
+
+def assert_same(tag, got, exp):
+    got = np.asarray(got)
+    exp = np.asarray(exp)
+    if got.shape != exp.shape or not np.array_equal(got, exp):
+        bad = np.argwhere(got != exp)
+        first = tuple(bad[0]) if len(bad) else None
+        detail = ""
+        if tag == "state" and first is not None:
+            env = first[0]
+            offs = sorted(set(int(b[1]) for b in bad if b[0] == env))
+            detail = f" env {env} bytes {[hex(o) for o in offs[:12]]} fields {sorted(set(_field(o) for o in offs))}"
+        raise AssertionError(f"{tag}: {len(bad)} mismatches, first at {first}{detail}")
+
+
+def pair(roms, env_rom, env_key=None, **cfg):
+    luma = synth.luma_table()
+    g = AtariEnv([r.data for r in roms], [(r.score_addr, r.gameover_addr) for r in roms], env_rom,
+                 luma=luma, env_key=env_key, **cfg)
+    ocfg = {k: v for k, v in cfg.items() if k in ("frameskip", "sticky", "n_cache", "startup_frames", "max_noops",
+                                                  "output_mode", "seed")}
+    o = OracleEnvs([r.data for r in roms], [r.score_addr for r in roms], [r.gameover_addr for r in roms],
+                   env_rom, luma=luma, env_key=env_key, **ocfg)
+    return g, o
+
+
+def run_parity(g, o, actions, check_frames=False, check_state_every=1, n_threads=8):
+    n = g.n
+    assert_same("state", g.state().cpu().numpy(), o.state())
+    for s in range(actions.shape[0]):
+        a = torch.from_numpy(actions[s]).cuda()
+        obs, rew, done = g.step(a)
+        oo, orw, od = o.step(actions[s], n_threads=n_threads)
+        torch.cuda.synchronize()
+        assert_same(f"step {s} rewards", rew.cpu().numpy(), orw)
+        assert_same(f"step {s} dones", done.cpu().numpy(), od)
+        assert_same(f"step {s} obs", obs.cpu().numpy(), oo)
+        if check_frames:
+            assert_same(f"step {s} frames", g.frames().cpu().numpy(), o.frames())
+        if s % check_state_every == 0 or s == actions.shape[0] - 1:
+            assert_same("state", g.state().cpu().numpy(), o.state())
+    return n
+
+
+def test_cache_matches_oracle():
+    for w_roms in (synth.workload(2, n_envs=8).roms, synth.workload(3, n_envs=32).roms,
+                   [synth.fuzz_rom(s, jam=s % 2 == 0) for s in range(4)]):
+        g, o = pair(w_roms, [0], seed=7)
+        assert_same("cache", g.cache().cpu().numpy(), o.cache())
+
+
+def test_playfield_full_tiny_config():
+    """16 envs of one 4 KB playfield cartridge, 250 steps x 4 frames, palette
+    frames out: every output and both rendered frames at every step."""
+    w = synth.workload(1)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_PALETTE, seed=w.seed, form=FORM_PLAIN)
+    acts = synth.actions(11, w.steps, w.n_envs)
+    run_parity(g, o, acts, check_frames=True)
+
+
+def test_sprite_family_stack_output():
+    """Eight sprite cartridges (players, missiles, ball, HMOVE, collision-driven
+    score), 96 envs (one partial block), full preprocessing to the 84x84x4 stack."""
+    w = synth.workload(2, n_envs=96)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=w.seed)
+    acts = synth.actions(12, 120, 96)
+    run_parity(g, o, acts, check_frames=True, check_state_every=1)
+
+
+def test_banked_sticky_family():
+    """32 cartridges mixing 4 KB, F8 and F6 with code in every bank, RIOT-timer
+    frame timing and sticky actions drawn from the per-env Philox stream."""
+    w = synth.workload(3, n_envs=64)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, sticky=True, seed=w.seed)
+    acts = synth.actions(13, 80, 64)
+    run_parity(g, o, acts, check_frames=True)
+
+
+@pytest.mark.parametrize("seed0", [0, 8])
+def test_fuzz_programs(seed0):
+    """Random-program cartridges (all documented opcodes, decimal mode, RMW on
+    TIA strobes, TIA/RIOT reads, halting opcodes) stepped on both sides."""
+    roms = [synth.fuzz_rom(seed0 + s, jam=s % 3 == 0) for s in range(8)]
+    env_rom = [i % 8 for i in range(64)]
+    g, o = pair(roms, env_rom, output_mode=OUT_STACK, seed=5)
+    acts = synth.actions(14 + seed0, 60, 64)
+    run_parity(g, o, acts, check_frames=True)
+
+
+def test_full_size_sprite_config_sampled():
+    """The 4096-env, 8-ROM configuration in the plain form: 25 steps, all envs
+    free of faults, and 40 sampled envs (their own env keys) equal to the
+    oracle run on just those envs."""
+    w = synth.workload(2)
+    n = w.n_envs
+    luma = synth.luma_table()
+    g = AtariEnv.from_workload(w, form=FORM_PLAIN)
+    rng = np.random.default_rng(3)
+    idx = np.sort(rng.choice(n, 40, replace=False))
+    o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
+                   [w.env_rom[i] for i in idx], luma=luma, env_key=idx, seed=w.seed)
+    acts = synth.actions(15, 25, n)
+    for s in range(25):
+        obs, rew, done = g.step(torch.from_numpy(acts[s]).cuda())
+        oo, orw, od = o.step(acts[s][idx], n_threads=8)
+        assert_same(f"step {s} rewards", rew.cpu().numpy()[idx], orw)
+        assert_same(f"step {s} dones", done.cpu().numpy()[idx], od)
+        assert_same(f"step {s} obs", obs.cpu().numpy()[idx], oo)
+    assert_same("state", g.state().cpu().numpy()[idx], o.state())
+    assert int(g.status().abs().sum().item()) == 0
+
+
+@pytest.mark.parametrize("n", [1, 37])
+def test_ragged_and_single(n):
+    w = synth.workload(2, n_envs=n)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=9)
+    run_parity(g, o, synth.actions(16, 30, n), check_frames=True)
+
+
+def test_zero_envs():
+    w = synth.workload(1, n_envs=1)
+    g = AtariEnv([w.roms[0].data], [(0x80, 0x81)], [], luma=synth.luma_table())
+    a = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    g.step(a)
+    assert g.state().shape == (0, 256)
+
+
+def test_bad_actions_flag_status_and_act_as_noop():
+    w = synth.workload(1, n_envs=4)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_PALETTE, seed=1)
+    acts = np.array([[0, 18, 255, 3]] * 5, np.uint8)
+    run_parity(g, o, acts)
+    st = g.status().cpu().numpy()
+    assert list(st & ST_BAD_ACTION) == [0, ST_BAD_ACTION, ST_BAD_ACTION, 0]
+
+
+def test_log_overflow_is_reported():
+    """A sprite cartridge writes several hundred TIA registers per frame; a
+    256-entry log overflows and the env's status says so (the rendered frame
+    is then not exact; nothing else is affected)."""
+    w = synth.workload(2, n_envs=8)
+    g = AtariEnv.from_workload(w, log_cap=256)
+    g.step(torch.zeros(8, dtype=torch.uint8, device="cuda"))
+    assert ((g.status().cpu().numpy() & ST_LOG_OVERFLOW) != 0).all()
+
+
+def test_state_roundtrip_resumes_exactly():
+    w = synth.workload(3, n_envs=32)
+    a = AtariEnv.from_workload(w)
+    b = AtariEnv.from_workload(w)
+    acts = synth.actions(17, 20, 32)
+    for s in range(10):
+        a.step(torch.from_numpy(acts[s]).cuda())
+    b.set_state(a.state())
+    # the obs stack is not part of the machine state: compare rewards, dones, state
+    for s in range(10, 20):
+        _, ra, da = a.step(torch.from_numpy(acts[s]).cuda())
+        _, rb, db = b.step(torch.from_numpy(acts[s]).cuda())
+        assert torch.equal(ra, rb) and torch.equal(da, db)
+    assert torch.equal(a.state(), b.state())
+
+
+def test_reset_mask_matches_oracle():
+    w = synth.workload(2, n_envs=16)
+    g, o = pair(w.roms, w.env_rom, seed=4)
+    acts = synth.actions(18, 6, 16)
+    run_parity(g, o, acts[:3])
+    mask = (np.arange(16) % 3 == 0).astype(np.uint8)
+    g.reset(torch.from_numpy(mask).cuda())
+    o.reset(mask)
+    run_parity(g, o, acts[3:])
+
+
+def test_host_step_matches_device_step():
+    w = synth.workload(2, n_envs=64)
+    a = AtariEnv.from_workload(w)
+    b = AtariEnv.from_workload(w)
+    acts = synth.actions(19, 8, 64)
+    for s in range(8):
+        oa, ra, da = a.step(torch.from_numpy(acts[s]).cuda())
+        ob, rb, db = b.step_host(acts[s])
+        assert np.array_equal(oa.cpu().numpy(), ob) and np.array_equal(ra.cpu().numpy(), rb)
+        assert np.array_equal(da.cpu().numpy(), db)
