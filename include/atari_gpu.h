@@ -80,13 +80,16 @@ typedef struct {
     int output_mode;      /* ATARI_OUT_* */
     int form;             /* ATARI_FORM_* */
     int log_cap;          /* TIA-write log entries per rendered frame (>= 256; default 4096) */
-    int envs_per_block;   /* interpreter threads per block (batched form; 0 = autotune) */
+    int envs_per_block;   /* batched form: envs per interpreter block, <= 128 (0 = autotune) */
+    int envs_per_warp;    /* batched form: envs per warp, 1..32 (0 = autotune); fewer than 32 trades
+                             SIMT width for more independent instruction streams on small batches */
+    int raster_warps_per_frame; /* batched form: warps rendering one frame, 1..4 (0 = autotune) */
     uint64_t seed;        /* Philox4x32-10 key for start states, resets and sticky draws */
 } atari_config;
 
 /* Fill *cfg with the paper's defaults: F = 4, no sticky actions, 30 cached
- * states, 64 start-up frames, up to 30 no-ops, stack output, batched form,
- * log_cap 4096, autotuned block size, seed 1. */
+ * states, 64 start-up frames, up to 30 no-ops, stack output, plain form,
+ * log_cap 4096, autotuned launch shapes, seed 1. */
 ATARI_API void atari_default_config(atari_config *cfg);
 
 /*
@@ -187,6 +190,12 @@ ATARI_API int atari_env_counters(atari_env *env, uint64_t *instructions, uint64_
 #define ATARI_PROF_COPY 4       /* output copies */
 ATARI_API int atari_env_profile(atari_env *env, int enable);
 ATARI_API int atari_env_profile_read(atari_env *env, double *ms, uint64_t *launches);
+
+/* Launch shape in use (batched form: the autotuned or configured values;
+ * plain form: 32 envs per warp, 128 per block, 1 warp per frame, and the
+ * grid of the interpreter launch).  Host pointers; any may be NULL. */
+ATARI_API int atari_env_launch_shape(atari_env *env, int *envs_per_warp, int *envs_per_block,
+                                     int *raster_warps_per_frame, int *grid);
 
 /* Number of envs, and the bytes of device memory the env holds. */
 ATARI_API int atari_env_info(atari_env *env, int *n_envs, size_t *device_bytes);

@@ -19,6 +19,7 @@
 #include "../../include/atari_gpu.h"
 #include "device_machine.cuh"
 #include "render.cuh"
+#include "batched.cuh"
 
 using namespace atari;
 
@@ -325,9 +326,10 @@ __global__ void __launch_bounds__(128) k_interp_plain(StepArgs a) {
   if (!a.done_int[i]) m.store(st);
 }
 
-// Rasteriser: one warp per (env, slot) frame.
+// Rasteriser: one warp per (env, slot) frame; frame (i, slot) goes to
+// out + i * env_stride + (slot - first_slot) * 33600.
 __global__ void __launch_bounds__(128) k_raster(const uint32_t *log, const uint8_t *snap, const uint32_t *meta,
-                                                uint8_t *frames, int n, int first_slot, int log_cap) {
+                                                uint8_t *out, size_t env_stride, int n, int first_slot, int log_cap) {
   __shared__ __align__(16) uint8_t rows[4][160];
   const int warp = threadIdx.x >> 5;
   const int slots = 2 - first_slot;
@@ -339,7 +341,8 @@ __global__ void __launch_bounds__(128) k_raster(const uint32_t *log, const uint8
   R.load(snap + fs * 64);
   const uint32_t *mt = meta + fs * 2;
   uint32_t n_rec = mt[0] < (uint32_t)log_cap ? mt[0] : (uint32_t)log_cap;
-  render_frame_warp(R, log + fs * log_cap, n_rec, mt[1], rows[warp], frames + fs * (FRAME_H * FRAME_W));
+  render_frame_warp(R, log + fs * log_cap, n_rec, mt[1], rows[warp],
+                    out + (size_t)i * env_stride + (size_t)(slot - first_slot) * (FRAME_H * FRAME_W));
 }
 
 // Preprocessing: one block per env.  Luma of both frames, pixelwise maximum,
@@ -456,6 +459,17 @@ struct atari_env {
   uint32_t *d_ctr = nullptr;
   uint8_t *d_act = nullptr;   // staging for atari_env_step_host
   uint8_t *d_obs_tmp = nullptr;
+  // batched form
+  uint32_t *d_romw = nullptr;       // [n_roms][16384] staged-ROM words
+  uint8_t *d_dec_op = nullptr;      // 512 bytes
+  int32_t *d_grp = nullptr;         // rom, start, count per work item (3 * n_groups) then perm (n)
+  int *d_queue = nullptr;
+  int n_groups = 0, lanes = 32, warps = 4, wpf = 4, grid = 0, romw_words = 4096, max_blocks = 1;
+  std::vector<int32_t> h_env_rom;
+  std::vector<uint32_t> h_banks;
+  cudaStream_t cap_stream = nullptr;
+  struct GraphEntry { const void *k[4]; cudaGraphExec_t exec; };
+  std::vector<GraphEntry> graphs;
   // profiling: (slot, start, end) event triples of the launches since the last read
   bool profiling = false;
   struct Rec { int slot; cudaEvent_t a, b; };
@@ -484,11 +498,104 @@ int validate(const atari_config &c) {
   if (c.form != ATARI_FORM_PLAIN && c.form != ATARI_FORM_BATCHED) return fail(ATARI_EINVAL, "bad form");
   if (c.log_cap < 256 || c.log_cap > (1 << 20)) return fail(ATARI_EINVAL, "log_cap must be in 256..2^20");
   if (c.sticky != 0 && c.sticky != 1) return fail(ATARI_EINVAL, "sticky must be 0 or 1");
+  if (c.envs_per_block < 0 || c.envs_per_block > 128 || c.envs_per_warp < 0 || c.envs_per_warp > 32 ||
+      c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4)
+    return fail(ATARI_EINVAL, "envs_per_block must be 0..128, envs_per_warp 0..32, raster_warps_per_frame 0..4");
   return 0;
 }
 
 }  // namespace
 
+
+namespace {
+
+// Envs grouped by cartridge into work items of E envs (ascending env index
+// within a cartridge); uploads rom/start/count per item and the permutation.
+int build_groups(atari_env *E, int lanes, int warps) {
+  const int per = lanes * warps;
+  std::vector<int32_t> rom, start, count, perm;
+  perm.reserve(E->n);
+  for (int r = 0; r < E->n_roms; ++r) {
+    int first = (int)perm.size();
+    for (int i = 0; i < E->n; ++i)
+      if (E->h_env_rom[i] == r) perm.push_back(i);
+    for (int s = first; s < (int)perm.size(); s += per) {
+      rom.push_back(r);
+      start.push_back(s);
+      count.push_back(std::min(per, (int)perm.size() - s));
+    }
+  }
+  const int ng = (int)rom.size();
+  std::vector<int32_t> blob;
+  blob.insert(blob.end(), rom.begin(), rom.end());
+  blob.insert(blob.end(), start.begin(), start.end());
+  blob.insert(blob.end(), count.begin(), count.end());
+  blob.insert(blob.end(), perm.begin(), perm.end());
+  if (E->d_grp) cudaFree(E->d_grp);
+  E->d_grp = nullptr;
+  size_t dummy = 0;
+  if (int rc = dalloc(&E->d_grp, std::max<size_t>(blob.size(), 1) * 4, dummy)) return rc;
+  CUDA_TRY(cudaMemcpy(E->d_grp, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice));
+  E->n_groups = ng;
+  E->lanes = lanes;
+  E->warps = warps;
+  size_t smem = (size_t)E->romw_words * 4 + 512 + (size_t)lanes * warps * (512 + TIA_BYTES);
+  int per_sm = 0;
+  CUDA_TRY(cudaFuncSetAttribute(k_interp_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched, warps * 32, smem));
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device));
+  E->max_blocks = std::max(1, per_sm) * sms;
+  E->grid = std::max(1, std::min(ng, E->max_blocks));
+  for (auto &g : E->graphs) cudaGraphExecDestroy(g.exec);
+  E->graphs.clear();
+  return 0;
+}
+
+BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards, uint8_t *d_dones) {
+  const atari_config &c = E->cfg;
+  BatchArgs a;
+  a.state = E->d_state;
+  a.cache = E->d_cache;
+  a.romw = E->d_romw;
+  a.info = E->d_info;
+  a.dec_op = E->d_dec_op;
+  a.actions = d_actions;
+  a.rew_int = E->d_rew;
+  a.done_int = E->d_done;
+  a.rew_out = d_rewards;
+  a.done_out = d_dones;
+  a.log = E->d_log;
+  a.snap = E->d_snap;
+  a.meta = E->d_meta;
+  a.counters = E->d_ctr;
+  a.grp_rom = E->d_grp;
+  a.grp_start = E->d_grp + E->n_groups;
+  a.grp_count = E->d_grp + 2 * E->n_groups;
+  a.perm = E->d_grp + 3 * E->n_groups;
+  a.queue = E->d_queue;
+  a.n_groups = E->n_groups;
+  a.lanes = E->lanes;
+  a.E = E->lanes * E->warps;
+  a.romw_words = E->romw_words;
+  a.frameskip = c.frameskip;
+  a.sticky = c.sticky;
+  a.n_cache = c.n_cache;
+  a.log_cap = c.log_cap;
+  a.first_slot = c.output_mode == ATARI_OUT_PALETTE ? 1 : 0;
+  a.seed = c.seed;
+  return a;
+}
+
+size_t interp_smem(const atari_env *E) {
+  return (size_t)E->romw_words * 4 + 512 + (size_t)E->lanes * E->warps * (512 + TIA_BYTES);
+}
+size_t fused_smem() { return 2 * 210 * 160 + 128 + 7056; }
+
+struct ProfScope;  // defined below
+int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vector<uint32_t> &dec);
+
+}  // namespace
 namespace {
 cudaEvent_t take_event(atari_env *E) {
   if (!E->pool.empty()) {
@@ -536,6 +643,8 @@ void atari_default_config(atari_config *c) {
   c->form = ATARI_FORM_PLAIN;
   c->log_cap = 4096;
   c->envs_per_block = 0;
+  c->envs_per_warp = 0;
+  c->raster_warps_per_frame = 0;
   c->seed = 1;
 }
 
@@ -550,7 +659,8 @@ size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg) {
   b += (size_t)n_roms * cfg->n_cache * 256;               // cache
   b += n * 2 * (size_t)cfg->log_cap * 4;                  // log
   b += n * 2 * 64 + n * 2 * 2 * 4;                        // snapshots, meta
-  b += n * 2 * 210 * 160;                                 // frames (plain form)
+  if (cfg->form == ATARI_FORM_PLAIN) b += n * 2 * 210 * 160;   // frames (plain form only)
+  else b += (size_t)n_roms * 16384 * 4 + 512 + n * 4 + 64;     // staged-ROM words, work items
   if (cfg->output_mode == ATARI_OUT_STACK) b += n * 4 * 7056 + n;
   b += n * (4 + 1 + 8 + 1);                               // rewards, dones, counters, action staging
   return b;
@@ -594,7 +704,8 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
       (rc = dalloc(&E->d_env_key, n * 4, T)) || (rc = dalloc(&E->d_state, n * 256, T)) ||
       (rc = dalloc(&E->d_cache, (size_t)n_roms * c.n_cache * 256, T)) ||
       (rc = dalloc(&E->d_log, n * 2 * (size_t)c.log_cap * 4, T)) || (rc = dalloc(&E->d_snap, n * 2 * 64, T)) ||
-      (rc = dalloc(&E->d_meta, n * 2 * 2 * 4, T)) || (rc = dalloc(&E->d_frames, n * 2 * 210 * 160, T)) ||
+      (rc = dalloc(&E->d_meta, n * 2 * 2 * 4, T)) ||
+      (c.form == ATARI_FORM_PLAIN && (rc = dalloc(&E->d_frames, n * 2 * 210 * 160, T))) ||
       (rc = dalloc(&E->d_rew, n * 4, T)) || (rc = dalloc(&E->d_done, n, T)) || (rc = dalloc(&E->d_ctr, n * 8, T)) ||
       (rc = dalloc(&E->d_act, n, T)) || (rc = dalloc(&E->d_luma, 128, T)))
     return bail(rc);
@@ -615,7 +726,8 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
       memcpy(dst, roms[r], rom_sizes[r]);
     }
     info[r] = (uint32_t)scheme_of(rom_sizes[r]) | (uint32_t)(meta[r].score_addr & 0x7F) << 8 |
-              (uint32_t)(meta[r].gameover_addr & 0x7F) << 16;
+              (uint32_t)(meta[r].gameover_addr & 0x7F) << 16 |
+              (uint32_t)(rom_sizes[r] <= 4096 ? 1u : rom_sizes[r] / 4096) << 24;
     // power-on state: registers and RAM zero, SP $FD, P $24, PC from the reset
     // vector of bank 0, timer 0 with interval 1024 written at cycle 0
     uint8_t *p = power.data() + (size_t)r * 256;
@@ -627,6 +739,9 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
     for (int b = 0; b < 8; ++b) p[S::BAR_LINE + b] = 0xFF;
   }
   std::vector<uint32_t> dec = build_decode_table();
+  E->h_env_rom.assign(env_rom, env_rom + n);
+  E->h_banks.resize(n_roms);
+  for (int r = 0; r < n_roms; ++r) E->h_banks[r] = rom_sizes[r] <= 4096 ? 1u : (uint32_t)(rom_sizes[r] / 4096);
   std::vector<uint32_t> keys(n);
   for (size_t i = 0; i < n; ++i) keys[i] = env_key ? env_key[i] : (uint32_t)i;
 
@@ -665,14 +780,8 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
   cudaFree(d_work);
   cudaFree(d_snaps);
   if (rc) return bail(rc);
-  if (c.output_mode == ATARI_OUT_STACK) {
-    static bool attr_set = false;
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
-      attr_set = true;
-    }
+  if (c.form == ATARI_FORM_BATCHED) {
+    if ((rc = setup_batched(E, img, dec))) return bail(rc);
   }
   *out = E;
   return 0;
@@ -682,7 +791,9 @@ void atari_env_destroy(atari_env *E) {
   if (!E) return;
   void *ptrs[] = {E->d_roms, E->d_info, E->d_dec, E->d_env_rom, E->d_env_key, E->d_state, E->d_cache, E->d_log,
                   E->d_snap, E->d_meta, E->d_frames, E->d_ring, E->d_head, E->d_luma, E->d_rew, E->d_done,
-                  E->d_ctr, E->d_act, E->d_obs_tmp};
+                  E->d_ctr, E->d_act, E->d_obs_tmp, E->d_romw, E->d_dec_op, E->d_grp, E->d_queue};
+  for (auto &g : E->graphs) cudaGraphExecDestroy(g.exec);
+  if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &r : E->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -701,13 +812,12 @@ int atari_env_reset(atari_env *E, const uint8_t *d_mask, atari_stream stream) {
   return 0;
 }
 
-int atari_env_step(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32_t *d_rewards, uint8_t *d_dones,
-                   atari_stream stream) {
-  g_err.clear();
-  if (!E) return fail(ATARI_EINVAL, "env is NULL");
-  if (E->n == 0) return 0;
-  if (!d_actions) return fail(ATARI_EINVAL, "d_actions is NULL");
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+int step_plain(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32_t *d_rewards, uint8_t *d_dones,
+               cudaStream_t s) {
   const atari_config &c = E->cfg;
   StepArgs a;
   a.state = E->d_state;
@@ -739,8 +849,8 @@ int atari_env_step(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
   long long warps = (long long)E->n * 2;
   {
     ProfScope p(E, ATARI_PROF_RASTER, s);
-    k_raster<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(E->d_log, E->d_snap, E->d_meta, E->d_frames, E->n, 0,
-                                                          c.log_cap);
+    k_raster<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(E->d_log, E->d_snap, E->d_meta, E->d_frames,
+                                                          (size_t)2 * 210 * 160, E->n, 0, c.log_cap);
   }
   CUDA_TRY(cudaGetLastError());
   if (c.output_mode == ATARI_OUT_STACK) {
@@ -756,6 +866,195 @@ int atari_env_step(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
                                cudaMemcpyDeviceToDevice, s));
   }
   return 0;
+}
+
+
+// Batched form: reset the work queue, persistent interpreter, then the fused
+// replay + preprocessing (stack output) or the replay of frame F straight
+// into the observation (palette output).
+int launch_batched(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32_t *d_rewards, uint8_t *d_dones,
+                   cudaStream_t s) {
+  const atari_config &c = E->cfg;
+  BatchArgs a = batch_args(E, d_actions, d_rewards, d_dones);
+  CUDA_TRY(cudaMemsetAsync(E->d_queue, 0, sizeof(int), s));
+  {
+    ProfScope p(E, ATARI_PROF_INTERP, s);
+    k_interp_batched<<<E->grid, E->warps * 32, interp_smem(E), s>>>(a);
+  }
+  CUDA_TRY(cudaGetLastError());
+  if (c.output_mode == ATARI_OUT_STACK) {
+    ProfScope p(E, ATARI_PROF_FUSED, s);
+    k_raster_preprocess<<<E->n, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma, E->d_ring,
+                                                                E->d_head, E->d_done, d_obs, E->n, c.log_cap, E->wpf);
+  } else if (d_obs) {
+    ProfScope p(E, ATARI_PROF_RASTER, s);
+    k_raster<<<(unsigned)((E->n + 3) / 4), 128, 0, s>>>(E->d_log, E->d_snap, E->d_meta, d_obs, (size_t)210 * 160,
+                                                         E->n, 1, c.log_cap);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int step_batched(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32_t *d_rewards, uint8_t *d_dones,
+                 cudaStream_t s) {
+  if (E->profiling) return launch_batched(E, d_actions, d_obs, d_rewards, d_dones, s);
+  const void *key[4] = {d_actions, d_obs, d_rewards, d_dones};
+  cudaGraphExec_t exec = nullptr;
+  for (auto &g : E->graphs)
+    if (!memcmp(g.k, key, sizeof key)) exec = g.exec;
+  if (!exec) {
+    if (E->graphs.size() >= 4) {
+      cudaGraphExecDestroy(E->graphs.front().exec);
+      E->graphs.erase(E->graphs.begin());
+    }
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(E->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_batched(E, d_actions, d_obs, d_rewards, d_dones, E->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(E->cap_stream, &graph);
+    if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (ce != cudaSuccess) return fail(ATARI_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(ATARI_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    atari_env::GraphEntry ge;
+    memcpy(ge.k, key, sizeof key);
+    ge.exec = exec;
+    E->graphs.push_back(ge);
+  }
+  CUDA_TRY(cudaGraphLaunch(exec, s));
+  return 0;
+}
+
+
+// Time the batched interpreter on a copy of the current state and keep the
+// fastest (envs per warp, warps per block); then the fastest number of warps
+// per frame in the fused replay.  Every configuration computes the same
+// results; only speed differs.  The state, stack ring and heads are restored.
+int autotune(atari_env *E) {
+  const size_t n = (size_t)E->n;
+  uint8_t *st_bak = nullptr, *ring_bak = nullptr, *head_bak = nullptr;
+  size_t dummy = 0;
+  if (int rc = dalloc(&st_bak, n * 256, dummy)) return rc;
+  CUDA_TRY(cudaMemcpy(st_bak, E->d_state, n * 256, cudaMemcpyDeviceToDevice));
+  std::vector<uint8_t> acts(n);
+  uint32_t x = 0x9E3779B9u;
+  for (auto &v : acts) { x ^= x << 13; x ^= x >> 17; x ^= x << 5; v = (uint8_t)(x % 18u); }
+  CUDA_TRY(cudaMemcpy(E->d_act, acts.data(), n, cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cand[][2] = {{32, 4}, {32, 2}, {32, 1}, {16, 4}, {16, 2}, {8, 4}, {8, 2}, {4, 4}, {2, 4}, {1, 4}};
+  float best = 1e30f;
+  int bl = 32, bw = 4;
+  bool was_prof = E->profiling;
+  E->profiling = false;
+  for (auto &c : cand) {
+    if ((size_t)c[0] * c[1] > 4 * n && c[0] * c[1] > 32) continue;  // far more slots than envs
+    if (int rc = build_groups(E, c[0], c[1])) { cudaFree(st_bak); return rc; }
+    BatchArgs a = batch_args(E, E->d_act, nullptr, nullptr);
+    float t = 0;
+    for (int rep = 0; rep < 2; ++rep) {
+      CUDA_TRY(cudaMemcpy(E->d_state, st_bak, n * 256, cudaMemcpyDeviceToDevice));
+      CUDA_TRY(cudaMemset(E->d_queue, 0, sizeof(int)));
+      cudaEventRecord(e0);
+      k_interp_batched<<<E->grid, E->warps * 32, interp_smem(E)>>>(a);
+      cudaEventRecord(e1);
+      CUDA_TRY(cudaEventSynchronize(e1));
+      CUDA_TRY(cudaGetLastError());
+      cudaEventElapsedTime(&t, e0, e1);
+    }
+    if (t < best) { best = t; bl = c[0]; bw = c[1]; }
+  }
+  int rc = build_groups(E, bl, bw);
+  if (!rc && E->cfg.output_mode == ATARI_OUT_STACK) {
+    if (!(rc = dalloc(&ring_bak, n * 4 * 7056, dummy)) && !(rc = dalloc(&head_bak, n, dummy))) {
+      cudaMemcpy(ring_bak, E->d_ring, n * 4 * 7056, cudaMemcpyDeviceToDevice);
+      cudaMemcpy(head_bak, E->d_head, n, cudaMemcpyDeviceToDevice);
+      float fb = 1e30f;
+      for (int wpf : {1, 2, 4}) {
+        float t = 0;
+        for (int rep = 0; rep < 2; ++rep) {
+          cudaEventRecord(e0);
+          k_raster_preprocess<<<E->n, 64 * wpf, fused_smem()>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma, E->d_ring,
+                                                               E->d_head, E->d_done, nullptr, E->n, E->cfg.log_cap, wpf);
+          cudaEventRecord(e1);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&t, e0, e1);
+        }
+        if (t < fb) { fb = t; E->wpf = wpf; }
+      }
+      cudaMemcpy(E->d_ring, ring_bak, n * 4 * 7056, cudaMemcpyDeviceToDevice);
+      cudaMemcpy(E->d_head, head_bak, n, cudaMemcpyDeviceToDevice);
+    }
+  }
+  CUDA_TRY(cudaMemcpy(E->d_state, st_bak, n * 256, cudaMemcpyDeviceToDevice));
+  cudaError_t ce = cudaDeviceSynchronize();
+  cudaFree(st_bak);
+  if (ring_bak) cudaFree(ring_bak);
+  if (head_bak) cudaFree(head_bak);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  E->profiling = was_prof;
+  if (rc) return rc;
+  if (ce != cudaSuccess) return fail(ATARI_ECUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+  return 0;
+}
+
+int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vector<uint32_t> &dec) {
+  const int R = E->n_roms;
+  std::vector<uint32_t> words((size_t)R * 16384, 0u);
+  std::vector<uint8_t> dec_op(512, 0);
+  auto info_of = [&](uint32_t opc) {
+    uint32_t t = dec[opc];
+    return ((t >> 8) & 0xFu) | ((t >> 12) & 7u) << 4 | ((t >> 15) & 1u) << 7;
+  };
+  for (int o = 0; o < 256; ++o) {
+    dec_op[o] = (uint8_t)(dec[o] & 0xFF);
+    dec_op[256 + o] = (uint8_t)info_of((uint32_t)o);
+  }
+  uint32_t max_banks = 1;
+  for (int r = 0; r < R; ++r) {
+    const uint32_t banks = E->h_banks[r];
+    max_banks = std::max(max_banks, banks);
+    for (uint32_t b = 0; b < banks; ++b) {
+      const uint8_t *bk = img.data() + (size_t)r * ROM_SLOT + b * 4096;
+      for (uint32_t o = 0; o < 4096; ++o) {
+        uint32_t b0 = bk[o], b1 = o + 1 < 4096 ? bk[o + 1] : 0u, b2 = o + 2 < 4096 ? bk[o + 2] : 0u;
+        words[(size_t)r * 16384 + b * 4096 + o] = b0 | b1 << 8 | b2 << 16 | info_of(b0) << 24;
+      }
+    }
+  }
+  E->romw_words = (int)max_banks * 4096;
+  size_t &T = E->bytes;
+  if (int rc = dalloc(&E->d_romw, words.size() * 4, T)) return rc;
+  if (int rc = dalloc(&E->d_dec_op, 512, T)) return rc;
+  if (int rc = dalloc(&E->d_queue, 64, T)) return rc;
+  CUDA_TRY(cudaMemcpy(E->d_romw, words.data(), words.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(E->d_dec_op, dec_op.data(), 512, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaFuncSetAttribute(k_raster_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem()));
+  const atari_config &c = E->cfg;
+  if (c.envs_per_block > 0 && c.envs_per_warp > 0) {
+    int L = std::min(32, c.envs_per_warp), W = std::max(1, std::min(4, c.envs_per_block / L));
+    E->wpf = c.raster_warps_per_frame > 0 ? c.raster_warps_per_frame : 4;
+    return build_groups(E, L, W);
+  }
+  if (E->n == 0) return build_groups(E, 32, 4);
+  return autotune(E);
+}
+}  // namespace
+
+extern "C" {
+
+int atari_env_step(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32_t *d_rewards, uint8_t *d_dones,
+                   atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->n == 0) return 0;
+  if (!d_actions) return fail(ATARI_EINVAL, "d_actions is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (E->cfg.form == ATARI_FORM_BATCHED) return step_batched(E, d_actions, d_obs, d_rewards, d_dones, s);
+  return step_plain(E, d_actions, d_obs, d_rewards, d_dones, s);
 }
 
 int atari_env_step_host(atari_env *E, const uint8_t *actions, uint8_t *obs, int32_t *rewards, uint8_t *dones,
@@ -861,6 +1160,18 @@ int atari_env_profile_read(atari_env *E, double *ms, uint64_t *launches) {
     E->pool.push_back(r.b);
   }
   E->prof.clear();
+  return 0;
+}
+
+int atari_env_launch_shape(atari_env *E, int *envs_per_warp, int *envs_per_block, int *raster_warps_per_frame,
+                           int *grid) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  const bool b = E->cfg.form == ATARI_FORM_BATCHED;
+  if (envs_per_warp) *envs_per_warp = b ? E->lanes : 32;
+  if (envs_per_block) *envs_per_block = b ? E->lanes * E->warps : 128;
+  if (raster_warps_per_frame) *raster_warps_per_frame = b ? E->wpf : 1;
+  if (grid) *grid = b ? E->grid : (E->n + 127) / 128;
   return 0;
 }
 

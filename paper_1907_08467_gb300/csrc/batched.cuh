@@ -1,0 +1,301 @@
+// Batched form: persistent ROM-grouped interpreter and fused replay +
+// preprocessing.
+//
+// Interpreter: envs are grouped by cartridge into work items of E envs
+// (E = warps per block x envs per warp; a warp may run fewer than 32 envs,
+// which trades SIMT width for more independent instruction streams when the
+// batch is small).  Each block takes work items from an atomic queue, stages
+// the item's cartridge in shared memory when it differs from the one it
+// holds, and runs every env of the item for the whole step.
+//
+// Fused replay + preprocessing (the paper's TIA kernel with the rows of a
+// frame spread over several warps, followed by the agent's preprocessing):
+// one block per env renders frames F-1 and F into shared memory, takes the
+// pixelwise maximum of their lumas, resamples to 84x84 and pushes the plane
+// into the env's stack; frames never reach HBM.
+#pragma once
+#include <cstdint>
+
+#include "device_machine.cuh"
+#include "fast_console.cuh"
+#include "render.cuh"
+
+namespace atari {
+
+struct BatchArgs {
+  uint8_t *state;
+  const uint8_t *cache;
+  const uint32_t *romw;      // [n_roms][16384] staged-ROM words
+  const uint32_t *info;      // per ROM: scheme | score << 8 | gameover << 16 | banks << 24
+  const uint8_t *dec_op;     // 512 bytes: op per opcode, then mode/cycles/penalty per opcode
+  const uint8_t *actions;
+  int32_t *rew_int;
+  uint8_t *done_int;
+  int32_t *rew_out;
+  uint8_t *done_out;
+  uint32_t *log;
+  uint8_t *snap;
+  uint32_t *meta;
+  uint32_t *counters;
+  const int32_t *grp_rom, *grp_start, *grp_count, *perm;
+  int *queue;
+  int n_groups, lanes, E, romw_words;
+  int frameskip, sticky, n_cache, log_cap, first_slot;
+  uint64_t seed;
+};
+
+__device__ __forceinline__ void fast_reset_from_cache(uint8_t *st, const uint8_t *cache, uint32_t score,
+                                                      uint32_t rom, uint32_t n_cache, uint64_t seed,
+                                                      uint32_t env_key, uint32_t episode) {
+  uint32_t idx = scale32(philox_x0(seed, env_key, 0u, PURPOSE_RESET << 8, episode), n_cache);
+  const uint8_t *src = cache + ((size_t)rom * n_cache + idx) * 256;
+  const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+  uint4 *d4 = reinterpret_cast<uint4 *>(st);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) d4[i] = s4[i];
+#pragma unroll
+  for (int i = 8; i < 16; ++i) d4[i] = s4[i];
+  st[S::LAST_ACTION] = 0;
+  st[S::SCORE_PREV] = src[S::RAM + score];
+  *reinterpret_cast<uint32_t *>(st + S::EPISODE) = episode;
+}
+
+__device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i, const BatchArgs &a,
+                                              uint32_t rom, uint32_t score, uint32_t gameover) {
+  const uint32_t *ew = reinterpret_cast<const uint32_t *>(st + S::EPISODE);
+  uint32_t episode = ew[0], step_no = ew[1], env_key = ew[2], env_status = ew[3];
+  uint32_t last = st[S::LAST_ACTION];
+  uint32_t score_prev = st[S::SCORE_PREV];
+  uint32_t action = a.actions[i];
+  if (action >= 18) { env_status |= ST_BAD_ACTION; action = 0; }
+  int32_t reward = 0;
+  uint32_t log_total = 0;
+  const int F = a.frameskip;
+  for (int f = 1; f <= F; ++f) {
+    uint32_t act = action;
+    if (a.sticky) {
+      uint32_t u = philox_x0(a.seed, env_key, step_no, (uint32_t)f | PURPOSE_STICKY << 8, episode);
+      if (u < 0x40000000u) act = last;
+    }
+    last = act;
+    m.apply_action(act);
+    const int slot = f - (F - 1);
+    const bool logging = slot >= a.first_slot;
+    if (logging) {
+      m.snapshot(a.snap + ((size_t)i * 2 + slot) * 64);
+      m.logp = a.log + ((size_t)i * 2 + slot) * a.log_cap;
+      m.logn = 0;
+      m.logcap = (uint32_t)a.log_cap;
+    } else {
+      m.logp = nullptr;
+    }
+    const uint32_t lines = m.run_frame();
+    if (logging) {
+      uint32_t *mt = a.meta + ((size_t)i * 2 + slot) * 2;
+      mt[0] = m.logn;
+      mt[1] = lines;
+      log_total += m.logn;
+    }
+    const uint32_t s = m.ram[score * m.E];
+    reward += (int32_t)(int8_t)(uint8_t)(s - score_prev);
+    score_prev = s;
+  }
+  env_status |= m.status;
+  if (m.jam) env_status |= ST_ILLEGAL;
+  const uint32_t done = (m.ram[gameover * m.E] != 0 || m.jam) ? 1u : 0u;
+  a.rew_int[i] = reward;
+  a.done_int[i] = (uint8_t)done;
+  if (a.rew_out) a.rew_out[i] = reward;
+  if (a.done_out) a.done_out[i] = (uint8_t)done;
+  if (a.counters) {
+    a.counters[2 * i] = m.instret;
+    a.counters[2 * i + 1] = log_total;
+  }
+  uint32_t *ewo = reinterpret_cast<uint32_t *>(st + S::EPISODE);
+  ewo[1] = step_no + 1;
+  ewo[3] = env_status;
+  if (done) {
+    fast_reset_from_cache(st, a.cache, score, rom, (uint32_t)a.n_cache, a.seed, env_key, episode + 1);
+  } else {
+    m.store(st);
+    st[S::LAST_ACTION] = (uint8_t)last;
+    st[S::SCORE_PREV] = (uint8_t)score_prev;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t *romw = reinterpret_cast<uint32_t *>(smem);
+  uint8_t *dec_op = smem + (size_t)a.romw_words * 4;
+  uint32_t *ram = reinterpret_cast<uint32_t *>(dec_op + 512);
+  uint8_t *tia = reinterpret_cast<uint8_t *>(ram + 128 * a.E);
+  __shared__ int s_group;
+  for (int t = threadIdx.x; t < 512; t += blockDim.x) dec_op[t] = a.dec_op[t];
+  int cur_rom = -1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    __syncthreads();  // everyone is done with the previous item (ROM words, s_group)
+    if (threadIdx.x == 0) s_group = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int g = s_group;
+    if (g >= a.n_groups) break;
+    const int rom = a.grp_rom[g];
+    if (rom != cur_rom) {
+      const uint32_t banks = a.info[rom] >> 24;
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.romw + (size_t)rom * 16384);
+      uint4 *dst = reinterpret_cast<uint4 *>(romw);
+      for (uint32_t q = threadIdx.x; q < banks * 1024u; q += blockDim.x) dst[q] = src[q];
+      cur_rom = rom;
+      __syncthreads();
+    }
+    if (lane < a.lanes) {
+      const int j = warp * a.lanes + lane;
+      if (j < a.grp_count[g]) {
+        const int i = a.perm[a.grp_start[g] + j];
+        uint8_t *st = a.state + (size_t)i * 256;
+        const uint32_t inf = a.info[rom];
+        FastConsole m;
+        m.romw = romw;
+        m.dec_op = dec_op;
+        m.ram = ram + j;
+        m.tia = tia + j;
+        m.E = (uint32_t)a.E;
+        m.scheme = inf & 0xFF;
+        m.load(st);
+        fast_step_env(m, st, i, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
+      }
+    }
+  }
+}
+
+// Render rows [r0, r1) of one frame with one warp into a shared-memory frame.
+__device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uint32_t n_rec, uint32_t n_lines,
+                                        uint32_t r0, uint32_t r1, uint8_t *frame) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t ri = 0, base = 0;
+  uint32_t chunk = lane < n_rec ? recs[lane] : 0xFFFFFFFFu;
+  // records that take effect before the band's first row: apply only
+  const uint32_t start_clk = 228u * (WINDOW_Y0 + r0);
+  while (ri < n_rec) {
+    if (ri - base >= 32) {
+      base += 32;
+      chunk = base + lane < n_rec ? recs[base + lane] : 0xFFFFFFFFu;
+    }
+    const uint32_t rec = __shfl_sync(0xFFFFFFFFu, chunk, ri - base);
+    const uint32_t c = rec >> 14;
+    if (c >= start_clk) break;
+    R.apply((rec >> 8) & 0x3F, rec & 0xFF, c);
+    ++ri;
+  }
+  for (uint32_t r = r0; r < r1; ++r) {
+    uint8_t *row = frame + r * FRAME_W;
+    const uint32_t line = WINDOW_Y0 + r;
+    if (line >= n_lines) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) row[lane + 32 * k] = 0;
+      continue;
+    }
+    const uint32_t cl = 228u * line, end = cl + 228u;
+    uint32_t k = 0;
+    while (ri < n_rec) {
+      if (ri - base >= 32) {
+        base += 32;
+        chunk = base + lane < n_rec ? recs[base + lane] : 0xFFFFFFFFu;
+      }
+      const uint32_t rec = __shfl_sync(0xFFFFFFFFu, chunk, ri - base);
+      const uint32_t c = rec >> 14;
+      if (c >= end) break;
+      while (k < 5 && cl + 68u + lane + 32u * k < c) {
+        row[lane + 32 * k] = (uint8_t)R.pixel(lane + 32 * k, line);
+        ++k;
+      }
+      R.apply((rec >> 8) & 0x3F, rec & 0xFF, c);
+      ++ri;
+    }
+    for (; k < 5; ++k) row[lane + 32 * k] = (uint8_t)R.pixel(lane + 32 * k, line);
+  }
+}
+
+// One block per env: warps [0, W) render frame F-1, warps [W, 2W) frame F,
+// each warp a band of rows; then luma max, 84x84 area resampling, stack push.
+__global__ void __launch_bounds__(256) k_raster_preprocess(const uint32_t *log, const uint8_t *snap, const uint32_t *meta,
+                                                           const uint8_t *luma_g, uint8_t *ring, uint8_t *head,
+                                                           const uint8_t *done, uint8_t *obs, int n, int log_cap,
+                                                           int warps_per_frame) {
+  extern __shared__ __align__(16) uint8_t sm[];
+  uint8_t *fa = sm;                        // frame F-1, later the luma maximum
+  uint8_t *fb = sm + FRAME_H * FRAME_W;    // frame F
+  uint8_t *luma = fb + FRAME_H * FRAME_W;
+  uint8_t *plane = luma + 128;
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const int warp = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < 128; t += blockDim.x) luma[t] = luma_g[t];
+  if (warp < 2 * warps_per_frame) {
+    const int slot = warp / warps_per_frame, band = warp % warps_per_frame;
+    const uint32_t r0 = (uint32_t)(FRAME_H * band / warps_per_frame);
+    const uint32_t r1 = (uint32_t)(FRAME_H * (band + 1) / warps_per_frame);
+    const size_t fs = (size_t)i * 2 + slot;
+    RenderRegs R;
+    R.load(snap + fs * 64);
+    const uint32_t *mt = meta + fs * 2;
+    const uint32_t n_rec = mt[0] < (uint32_t)log_cap ? mt[0] : (uint32_t)log_cap;
+    render_rows_warp(R, log + fs * log_cap, n_rec, mt[1], r0, r1, slot ? fb : fa);
+  }
+  __syncthreads();
+  {
+    uint32_t *a4 = reinterpret_cast<uint32_t *>(fa);
+    const uint32_t *b4 = reinterpret_cast<const uint32_t *>(fb);
+    for (int q = threadIdx.x; q < FRAME_H * FRAME_W / 4; q += blockDim.x) {
+      uint32_t x = a4[q], y = b4[q], r = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t la = luma[((x >> (8 * k)) & 0xFF) >> 1], lb = luma[((y >> (8 * k)) & 0xFF) >> 1];
+        r |= (la > lb ? la : lb) << (8 * k);
+      }
+      a4[q] = r;
+    }
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 84 * 84; o += blockDim.x) {
+    uint32_t oi = o / 84, oj = o % 84;
+    uint32_t y0 = (5u * oi) >> 1;
+    uint32_t wy0 = (oi & 1) ? 42u : 84u, wy1 = 84u, wy2 = (oi & 1) ? 84u : 42u;
+    uint32_t x0, wx0, wx1, wx2;
+    col_weights(oj, x0, wx0, wx1, wx2);
+    const uint8_t *r0 = fa + y0 * FRAME_W + x0;
+    const uint8_t *r1 = r0 + FRAME_W;
+    const uint8_t *r2 = r1 + FRAME_W;
+    uint32_t rs0 = wx0 * r0[0] + wx1 * r0[1] + (wx2 ? wx2 * r0[2] : 0u);
+    uint32_t rs1 = wx0 * r1[0] + wx1 * r1[1] + (wx2 ? wx2 * r1[2] : 0u);
+    uint32_t rs2 = wx0 * r2[0] + wx1 * r2[1] + (wx2 ? wx2 * r2[2] : 0u);
+    plane[o] = (uint8_t)((wy0 * rs0 + wy1 * rs1 + wy2 * rs2 + 16800u) / 33600u);
+  }
+  __syncthreads();
+  const uint32_t h = head[i];
+  uint8_t *rg = ring + (size_t)i * 4 * 7056;
+  const uint32_t *pl32 = reinterpret_cast<const uint32_t *>(plane);
+  if (obs) {
+    uint8_t *ob = obs + (size_t)i * 4 * 7056;
+    for (int s = 0; s < 3; ++s) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(rg + ((h + 1 + s) & 3) * 7056);
+      uint4 *dst = reinterpret_cast<uint4 *>(ob + s * 7056);
+      for (int q = threadIdx.x; q < 7056 / 16; q += blockDim.x) dst[q] = src[q];
+    }
+    const uint4 *p16 = reinterpret_cast<const uint4 *>(plane);
+    uint4 *dst = reinterpret_cast<uint4 *>(ob + 3 * 7056);
+    for (int q = threadIdx.x; q < 7056 / 16; q += blockDim.x) dst[q] = p16[q];
+  }
+  __syncthreads();
+  if (done[i]) {
+    uint4 *z = reinterpret_cast<uint4 *>(rg);
+    for (int q = threadIdx.x; q < 4 * 7056 / 16; q += blockDim.x) z[q] = make_uint4(0, 0, 0, 0);
+    if (threadIdx.x == 0) head[i] = 0;
+  } else {
+    uint32_t *dst = reinterpret_cast<uint32_t *>(rg + h * 7056);
+    for (int q = threadIdx.x; q < 7056 / 4; q += blockDim.x) dst[q] = pl32[q];
+    if (threadIdx.x == 0) head[i] = (uint8_t)((h + 1) & 3);
+  }
+}
+
+}  // namespace atari

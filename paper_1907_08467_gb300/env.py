@@ -27,7 +27,7 @@ class _Config(C.Structure):
     _fields_ = [("frameskip", C.c_int), ("sticky", C.c_int), ("n_cache", C.c_int),
                 ("startup_frames", C.c_int), ("max_noops", C.c_int), ("output_mode", C.c_int),
                 ("form", C.c_int), ("log_cap", C.c_int), ("envs_per_block", C.c_int),
-                ("seed", C.c_uint64)]
+                ("envs_per_warp", C.c_int), ("raster_warps_per_frame", C.c_int), ("seed", C.c_uint64)]
 
 
 class _Meta(C.Structure):
@@ -38,7 +38,7 @@ EXPORTS = ["atari_default_config", "atari_env_create", "atari_env_reset", "atari
            "atari_env_step_host", "atari_env_status", "atari_env_get_state", "atari_env_set_state",
            "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
            "atari_env_footprint", "atari_env_destroy", "atari_last_error", "atari_env_profile",
-           "atari_env_profile_read"]
+           "atari_env_profile_read", "atari_env_launch_shape"]
 PROF_SLOTS = 8
 PROF_NAMES = ["interpreter", "rasteriser", "preprocess", "fused_raster_preprocess", "copy", "s5", "s6", "s7"]
 
@@ -71,10 +71,11 @@ def load_library(path: str | None = None):
         L.atari_last_error.restype = C.c_char_p
         L.atari_env_profile.argtypes = [P, C.c_int]
         L.atari_env_profile_read.argtypes = [P, P, P]
+        L.atari_env_launch_shape.argtypes = [P, P, P, P, P]
         for name in ("atari_env_create", "atari_env_reset", "atari_env_step", "atari_env_step_host",
                      "atari_env_status", "atari_env_get_state", "atari_env_set_state",
                      "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
-                     "atari_env_profile", "atari_env_profile_read"):
+                     "atari_env_profile", "atari_env_profile_read", "atari_env_launch_shape"):
             getattr(L, name).restype = C.c_int
         if path is None:
             _lib = L
@@ -91,9 +92,10 @@ def _check(rc: int):
 
 
 def make_config(frameskip=4, sticky=False, n_cache=30, startup_frames=64, max_noops=30,
-                output_mode=OUT_STACK, form=FORM_PLAIN, log_cap=4096, envs_per_block=0, seed=1) -> _Config:
+                output_mode=OUT_STACK, form=FORM_PLAIN, log_cap=4096, envs_per_block=0, envs_per_warp=0,
+                raster_warps_per_frame=0, seed=1) -> _Config:
     return _Config(frameskip, int(sticky), n_cache, startup_frames, max_noops, output_mode, form,
-                   log_cap, envs_per_block, seed)
+                   log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed)
 
 
 def footprint(n_envs: int, n_roms: int, **cfg) -> int:
@@ -246,6 +248,12 @@ class AtariEnv:
         ln = (C.c_uint64 * PROF_SLOTS)()
         _check(self.lib.atari_env_profile_read(self.h, ms, ln))
         return {PROF_NAMES[k]: (ms[k], ln[k]) for k in range(PROF_SLOTS) if ln[k]}
+
+    def launch_shape(self):
+        """(envs per warp, envs per block, warps per frame, interpreter grid)."""
+        v = [C.c_int() for _ in range(4)]
+        _check(self.lib.atari_env_launch_shape(self.h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def info(self):
         n, b = C.c_int(), C.c_size_t()

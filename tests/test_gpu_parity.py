@@ -13,7 +13,8 @@ import torch
 
 from oracle import OracleEnvs
 from paper_1907_08467_gb300 import synth
-from paper_1907_08467_gb300.env import FORM_PLAIN, OUT_PALETTE, OUT_STACK, ST_BAD_ACTION, ST_LOG_OVERFLOW, AtariEnv
+from paper_1907_08467_gb300.env import (FORM_BATCHED, FORM_PLAIN, OUT_PALETTE, OUT_STACK, ST_BAD_ACTION,
+                                        ST_LOG_OVERFLOW, AtariEnv)
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +58,19 @@ def pair(roms, env_rom, env_key=None, **cfg):
     return g, o
 
 
+# Launch shapes exercised for the batched form: autotuned, and fixed
+# (envs per warp, envs per block, warps per frame) triples.
+FORMS = {
+    "plain": dict(form=FORM_PLAIN),
+    "batched-auto": dict(form=FORM_BATCHED),
+    "batched-32x128-w4": dict(form=FORM_BATCHED, envs_per_warp=32, envs_per_block=128, raster_warps_per_frame=4),
+    "batched-8x16-w1": dict(form=FORM_BATCHED, envs_per_warp=8, envs_per_block=16, raster_warps_per_frame=1),
+    "batched-1x4-w2": dict(form=FORM_BATCHED, envs_per_warp=1, envs_per_block=4, raster_warps_per_frame=2),
+}
+
+
 def run_parity(g, o, actions, check_frames=False, check_state_every=1, n_threads=8):
+    check_frames = check_frames and g.cfg.form == FORM_PLAIN
     n = g.n
     assert_same("state", g.state().cpu().numpy(), o.state())
     for s in range(actions.shape[0]):
@@ -82,52 +95,58 @@ def test_cache_matches_oracle():
         assert_same("cache", g.cache().cpu().numpy(), o.cache())
 
 
-def test_playfield_full_tiny_config():
+@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-1x4-w2"])
+def test_playfield_full_tiny_config(form):
     """16 envs of one 4 KB playfield cartridge, 250 steps x 4 frames, palette
-    frames out: every output and both rendered frames at every step."""
+    frames out: every output (and, in the plain form, both rendered frames)
+    at every step."""
     w = synth.workload(1)
-    g, o = pair(w.roms, w.env_rom, output_mode=OUT_PALETTE, seed=w.seed, form=FORM_PLAIN)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_PALETTE, seed=w.seed, **FORMS[form])
     acts = synth.actions(11, w.steps, w.n_envs)
     run_parity(g, o, acts, check_frames=True)
 
 
-def test_sprite_family_stack_output():
+@pytest.mark.parametrize("form", list(FORMS))
+def test_sprite_family_stack_output(form):
     """Eight sprite cartridges (players, missiles, ball, HMOVE, collision-driven
-    score), 96 envs (one partial block), full preprocessing to the 84x84x4 stack."""
+    score), 96 envs (ragged against every block size), full preprocessing to
+    the 84x84x4 stack."""
     w = synth.workload(2, n_envs=96)
-    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=w.seed)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=w.seed, **FORMS[form])
     acts = synth.actions(12, 120, 96)
     run_parity(g, o, acts, check_frames=True, check_state_every=1)
 
 
-def test_banked_sticky_family():
+@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-8x16-w1"])
+def test_banked_sticky_family(form):
     """32 cartridges mixing 4 KB, F8 and F6 with code in every bank, RIOT-timer
     frame timing and sticky actions drawn from the per-env Philox stream."""
     w = synth.workload(3, n_envs=64)
-    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, sticky=True, seed=w.seed)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, sticky=True, seed=w.seed, **FORMS[form])
     acts = synth.actions(13, 80, 64)
     run_parity(g, o, acts, check_frames=True)
 
 
-@pytest.mark.parametrize("seed0", [0, 8])
-def test_fuzz_programs(seed0):
+@pytest.mark.parametrize("seed0,form", [(0, "plain"), (8, "plain"), (0, "batched-auto"), (16, "batched-8x16-w1")])
+def test_fuzz_programs(seed0, form):
     """Random-program cartridges (all documented opcodes, decimal mode, RMW on
     TIA strobes, TIA/RIOT reads, halting opcodes) stepped on both sides."""
     roms = [synth.fuzz_rom(seed0 + s, jam=s % 3 == 0) for s in range(8)]
     env_rom = [i % 8 for i in range(64)]
-    g, o = pair(roms, env_rom, output_mode=OUT_STACK, seed=5)
+    g, o = pair(roms, env_rom, output_mode=OUT_STACK, seed=5, **FORMS[form])
     acts = synth.actions(14 + seed0, 60, 64)
     run_parity(g, o, acts, check_frames=True)
 
 
-def test_full_size_sprite_config_sampled():
-    """The 4096-env, 8-ROM configuration in the plain form: 25 steps, all envs
-    free of faults, and 40 sampled envs (their own env keys) equal to the
-    oracle run on just those envs."""
+@pytest.mark.parametrize("form", ["plain", "batched-auto"])
+def test_full_size_sprite_config_sampled(form):
+    """The 4096-env, 8-ROM configuration in the launch configuration the
+    benchmark times: 25 steps, all envs free of faults, and 40 sampled envs
+    (their own env keys) equal to the oracle run on just those envs."""
     w = synth.workload(2)
     n = w.n_envs
     luma = synth.luma_table()
-    g = AtariEnv.from_workload(w, form=FORM_PLAIN)
+    g = AtariEnv.from_workload(w, **FORMS[form])
     rng = np.random.default_rng(3)
     idx = np.sort(rng.choice(n, 40, replace=False))
     o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
@@ -143,16 +162,17 @@ def test_full_size_sprite_config_sampled():
     assert int(g.status().abs().sum().item()) == 0
 
 
-@pytest.mark.parametrize("n", [1, 37])
-def test_ragged_and_single(n):
+@pytest.mark.parametrize("n,form", [(1, "plain"), (37, "plain"), (1, "batched-auto"), (37, "batched-32x128-w4")])
+def test_ragged_and_single(n, form):
     w = synth.workload(2, n_envs=n)
-    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=9)
+    g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=9, **FORMS[form])
     run_parity(g, o, synth.actions(16, 30, n), check_frames=True)
 
 
-def test_zero_envs():
+@pytest.mark.parametrize("form", ["plain", "batched-auto"])
+def test_zero_envs(form):
     w = synth.workload(1, n_envs=1)
-    g = AtariEnv([w.roms[0].data], [(0x80, 0x81)], [], luma=synth.luma_table())
+    g = AtariEnv([w.roms[0].data], [(0x80, 0x81)], [], luma=synth.luma_table(), **FORMS[form])
     a = torch.zeros(0, dtype=torch.uint8, device="cuda")
     g.step(a)
     assert g.state().shape == (0, 256)
@@ -214,3 +234,19 @@ def test_host_step_matches_device_step():
         ob, rb, db = b.step_host(acts[s])
         assert np.array_equal(oa.cpu().numpy(), ob) and np.array_equal(ra.cpu().numpy(), rb)
         assert np.array_equal(da.cpu().numpy(), db)
+
+
+def test_batched_equals_plain_at_full_size():
+    """Both forms on the 4096-env configuration for 15 steps: identical
+    observations, rewards, dones and states (the autotuned launch shape
+    changes speed only)."""
+    w = synth.workload(2)
+    a = AtariEnv.from_workload(w, form=FORM_PLAIN)
+    b = AtariEnv.from_workload(w, form=FORM_BATCHED)
+    acts = synth.actions(21, 15, w.n_envs)
+    for s in range(15):
+        x = torch.from_numpy(acts[s]).cuda()
+        oa, ra, da = a.step(x)
+        ob, rb, db = b.step(x)
+        assert torch.equal(oa, ob) and torch.equal(ra, rb) and torch.equal(da, db), s
+    assert torch.equal(a.state(), b.state())
