@@ -207,6 +207,36 @@ ATARI_API size_t atari_env_footprint(int n_envs, int n_roms, const atari_config 
 /* Free everything; safe on NULL. */
 ATARI_API void atari_env_destroy(atari_env *env);
 
+/*
+ * Allocation-free step, for callers that cannot allocate device memory (a
+ * framework whose allocator owns every device buffer, or a fixed device
+ * memory budget): it calls no cudaMalloc/cudaFree.  The paper has no
+ * counterpart; it is a variant of the plain-form step above.
+ *
+ * Steps n_envs <= 64 envs of ONE cartridge (rom, host, rom_size bytes; meta
+ * gives its score and game-over RAM addresses).  d_state (device, n*256
+ * canonical states, in/out) is advanced one step of `frameskip` frames with
+ * d_actions (device, n bytes); every state's ROM index field is set to 0.
+ * d_cache (device, n_cache*256) holds the cartridge's start states (e.g. from
+ * atari_env_get_cache); finished envs are reset from it as in
+ * atari_env_step.  d_frame (device, n*210*160, may be NULL) receives frame F
+ * (palette values), d_rewards / d_dones (device, may be NULL) the rewards and
+ * dones.  Results equal atari_env_step of a plain-form env with palette
+ * output on the same states and actions.
+ *
+ * Its scratch (the cartridge image, TIA-write logs and frame records) is one
+ * fixed array of about 2.1 MB inside the library, held by every GPU that
+ * loads the library until the process exits.  n_envs above 64 returns
+ * ATARI_EINVAL.  The first call on a device looks up that array's device
+ * address; make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.
+ */
+ATARI_API int atari_step_noalloc(const uint8_t *rom, size_t rom_size, atari_rom_meta meta, uint8_t *d_state,
+                                 const uint8_t *d_cache, int n_cache, const uint8_t *d_actions, uint8_t *d_frame,
+                                 int32_t *d_rewards, uint8_t *d_dones, int n_envs, int frameskip, int sticky,
+                                 uint64_t seed, atari_stream stream);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 ATARI_API const char *atari_last_error(void);
 

@@ -1183,3 +1183,152 @@ int atari_env_info(atari_env *E, int *n_envs, size_t *device_bytes) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free step
+// For callers that cannot allocate device memory: code that runs under a
+// framework whose allocator owns every device buffer, or inside a region of
+// a fixed device-memory budget.  They pass their own state, start-state,
+// action and output buffers; everything else the step needs lives in the
+// file-scope array below, which every GPU that loads this library holds
+// until the process exits.
+namespace {
+constexpr int NA_MAX_ENVS = 64;
+constexpr int NA_LOG_CAP = 4096;
+constexpr size_t NA_ROM = 0;                                            // one cartridge, banks of 4 KB
+constexpr size_t NA_DEC = NA_ROM + ROM_SLOT;                            // 256-entry decode table
+constexpr size_t NA_INFO = NA_DEC + 1024;                               // cartridge info word
+constexpr size_t NA_REW = NA_INFO + 256;                                // rewards (internal copy)
+constexpr size_t NA_DONE = NA_REW + 4 * NA_MAX_ENVS;                    // dones (internal copy)
+constexpr size_t NA_CTR = NA_DONE + 256;                                // counters
+constexpr size_t NA_META = NA_CTR + 8 * NA_MAX_ENVS;                    // per frame: records, lines
+constexpr size_t NA_SNAP = NA_META + 16 * NA_MAX_ENVS;                  // per frame: 64-byte snapshot
+constexpr size_t NA_LOG = NA_SNAP + 128 * NA_MAX_ENVS;                  // per frame: TIA-write log
+constexpr size_t NA_BYTES = NA_LOG + (size_t)NA_MAX_ENVS * 2 * NA_LOG_CAP * 4;
+static __device__ __align__(256) uint8_t g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_na_mu;
+void *g_na_addr[64] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side name of the array is not a device address).
+int noalloc_scratch(uint8_t **out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(ATARI_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (!g_na_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(ATARI_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_na_addr[dev] = p;
+  }
+  *out = static_cast<uint8_t *>(g_na_addr[dev]);
+  return 0;
+}
+
+// Every env of this variant belongs to the one staged cartridge.
+__global__ void __launch_bounds__(128) k_interp_noalloc(StepArgs a) {
+  __shared__ uint32_t dec[256];
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) dec[t] = a.dec[t];
+  __syncthreads();
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  uint8_t *st = a.state + (size_t)i * 256;
+  st[S::ROM] = 0;
+  st[S::ROM + 1] = 0;
+  RomInfo ri = rom_info(a.info, 0);
+  Console<GlobalMem> m;
+  m.mem.ram = st + S::RAM;
+  m.mem.rom = a.roms;
+  m.dec = dec;
+  m.load(st);
+  m.scheme = ri.scheme;
+  step_env(m, st, i, a, ri);
+  if (!a.done_int[i]) m.store(st);
+}
+}  // namespace
+
+extern "C" int atari_step_noalloc(const uint8_t *rom, size_t rom_size, atari_rom_meta meta, uint8_t *d_state,
+                                  const uint8_t *d_cache, int n_cache, const uint8_t *d_actions, uint8_t *d_frame,
+                                  int32_t *d_rewards, uint8_t *d_dones, int n_envs, int frameskip, int sticky,
+                                  uint64_t seed, atari_stream stream) {
+  g_err.clear();
+  if (n_envs < 0 || n_envs > NA_MAX_ENVS)
+    return fail(ATARI_EINVAL, "atari_step_noalloc: n_envs must be in 0.." + std::to_string(NA_MAX_ENVS) +
+                                  " (the fixed scratch array holds at most that many envs)");
+  const int sc = scheme_of(rom_size);
+  if (!rom || sc < 0) return fail(ATARI_EINVAL, "atari_step_noalloc: ROM size must be 2048, 4096, 8192 or 16384");
+  if (meta.score_addr < 0x80 || meta.gameover_addr < 0x80)
+    return fail(ATARI_EINVAL, "atari_step_noalloc: score/game-over addresses must be in $80-$FF");
+  if (n_cache < 1 || n_cache > 64) return fail(ATARI_EINVAL, "atari_step_noalloc: n_cache must be in 1..64");
+  if (frameskip < 2 || frameskip > 16) return fail(ATARI_EINVAL, "atari_step_noalloc: frameskip must be in 2..16");
+  if (sticky != 0 && sticky != 1) return fail(ATARI_EINVAL, "atari_step_noalloc: sticky must be 0 or 1");
+  if (n_envs == 0) return 0;
+  if (!d_state || !d_cache || !d_actions) return fail(ATARI_EINVAL, "atari_step_noalloc: NULL buffer");
+  uint8_t *scr = nullptr;
+  if (int rc = noalloc_scratch(&scr)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // cartridge image (2K mirrored), decode table and info word, from host
+  // arrays that need no allocation
+  static uint8_t img[ROM_SLOT];
+  static uint32_t dec[256];
+  static uint32_t info[64];
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  memset(img, 0, sizeof img);
+  if (rom_size == 2048) {
+    memcpy(img, rom, 2048);
+    memcpy(img + 2048, rom, 2048);
+  } else {
+    memcpy(img, rom, rom_size);
+  }
+  for (int o = 0; o < 256; ++o) {
+    dec[o] = 0;
+    if (!OPMAP[o]) continue;
+    char mn[4] = {OPMAP[o][0], OPMAP[o][1], OPMAP[o][2], 0};
+    uint32_t op = 0, mode = 0;
+    for (uint32_t i = 0; i < sizeof(MNEMONICS) / sizeof(*MNEMONICS); ++i)
+      if (!strcmp(MNEMONICS[i], mn)) op = i;
+    for (uint32_t i = 0; i < sizeof(MODES) / sizeof(*MODES); ++i)
+      if (!strcmp(MODES[i], OPMAP[o] + 4)) mode = i;
+    bool pen;
+    uint32_t cyc = cycles_for(op, mode, pen);
+    dec[o] = op | mode << 8 | cyc << 12 | (pen ? 1u : 0u) << 15;
+  }
+  memset(info, 0, sizeof info);
+  info[0] = (uint32_t)sc | (uint32_t)(meta.score_addr & 0x7F) << 8 | (uint32_t)(meta.gameover_addr & 0x7F) << 16;
+  CUDA_TRY(cudaMemcpyAsync(scr + NA_ROM, img, sizeof img, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(scr + NA_DEC, dec, sizeof dec, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(scr + NA_INFO, info, sizeof info, cudaMemcpyHostToDevice, s));
+  // the previous call's frame records must not leak into this one
+  CUDA_TRY(cudaMemsetAsync(scr + NA_META, 0, NA_LOG - NA_META, s));
+  StepArgs a;
+  a.state = d_state;
+  a.cache = d_cache;
+  a.roms = scr + NA_ROM;
+  a.info = reinterpret_cast<const uint32_t *>(scr + NA_INFO);
+  a.dec = reinterpret_cast<const uint32_t *>(scr + NA_DEC);
+  a.actions = d_actions;
+  a.rew_int = reinterpret_cast<int32_t *>(scr + NA_REW);
+  a.done_int = scr + NA_DONE;
+  a.rew_out = d_rewards;
+  a.done_out = d_dones;
+  a.log = reinterpret_cast<uint32_t *>(scr + NA_LOG);
+  a.snap = scr + NA_SNAP;
+  a.meta = reinterpret_cast<uint32_t *>(scr + NA_META);
+  a.counters = reinterpret_cast<uint32_t *>(scr + NA_CTR);
+  a.n = n_envs;
+  a.frameskip = frameskip;
+  a.sticky = sticky;
+  a.n_cache = n_cache;
+  a.log_cap = NA_LOG_CAP;
+  a.first_slot = 1;
+  a.seed = seed;
+  k_interp_noalloc<<<(n_envs + 127) / 128, 128, 0, s>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  if (d_frame) {
+    k_raster<<<(unsigned)((n_envs + 3) / 4), 128, 0, s>>>(a.log, a.snap, a.meta, d_frame, (size_t)210 * 160, n_envs, 1,
+                                                          NA_LOG_CAP);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return 0;
+}

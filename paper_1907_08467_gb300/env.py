@@ -38,7 +38,7 @@ EXPORTS = ["atari_default_config", "atari_env_create", "atari_env_reset", "atari
            "atari_env_step_host", "atari_env_status", "atari_env_get_state", "atari_env_set_state",
            "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
            "atari_env_footprint", "atari_env_destroy", "atari_last_error", "atari_env_profile",
-           "atari_env_profile_read", "atari_env_launch_shape"]
+           "atari_env_profile_read", "atari_env_launch_shape", "atari_step_noalloc"]
 PROF_SLOTS = 8
 PROF_NAMES = ["interpreter", "rasteriser", "preprocess", "fused_raster_preprocess", "copy", "s5", "s6", "s7"]
 
@@ -72,6 +72,9 @@ def load_library(path: str | None = None):
         L.atari_env_profile.argtypes = [P, C.c_int]
         L.atari_env_profile_read.argtypes = [P, P, P]
         L.atari_env_launch_shape.argtypes = [P, P, P, P, P]
+        L.atari_step_noalloc.argtypes = [P, C.c_size_t, _Meta, P, P, C.c_int, P, P, P, P, C.c_int, C.c_int,
+                                         C.c_int, C.c_uint64, P]
+        L.atari_step_noalloc.restype = C.c_int
         for name in ("atari_env_create", "atari_env_reset", "atari_env_step", "atari_env_step_host",
                      "atari_env_status", "atari_env_get_state", "atari_env_set_state",
                      "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
