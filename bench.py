@@ -32,11 +32,14 @@ METRIC = "raw emulated frames/sec on 1 GB300 vs plain GPU path and CPU oracle; p
 SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 
 # Warp instructions issued per env-frame by the interpreter kernel on the
-# default workload, from the ncu capture summarised in profiles/ (metric
-# sm__inst_executed.sum divided by the env-frames of the captured launch).
-# Refresh whenever the interpreter changes; None means not yet measured.
-INTERP_WARP_INST_PER_ENV_FRAME = {"plain": None, "batched": None}
-INTERP_DRAM_BYTES_PER_ENV_STEP = {"plain": None, "batched": None}
+# default workload (sprite, 4096 envs) and DRAM bytes per env-step, from the
+# ncu capture summarised in profiles/interpreter_batched_sprite4096.md
+# (smsp__inst_executed.sum and dram__bytes_read.sum + dram__bytes_write.sum
+# of one launch, divided by its 16384 env-frames / 4096 env-steps), keyed by
+# (form, envs per warp).  Refresh whenever the interpreter changes; a shape
+# without an entry reports achieved = null.
+INTERP_WARP_INST_PER_ENV_FRAME = {("batched", 4): 5278237589 / 16384}
+INTERP_DRAM_BYTES_PER_ENV_STEP = {("batched", 4): (4978432 + 475136) / 4096}
 
 
 def parse():
@@ -45,7 +48,7 @@ def parse():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--form", default="plain", choices=["plain", "batched"])
+    p.add_argument("--form", default="batched", choices=["plain", "batched"])
     p.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5])
     p.add_argument("--n-envs", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -319,10 +322,11 @@ def main():
     roof = None
     if interp_n:
         dur = interp_ms / interp_n / 1000.0
-        per = INTERP_WARP_INST_PER_ENV_FRAME.get(args.form)
+        shape_key = (args.form, env.launch_shape()[0])
+        per = INTERP_WARP_INST_PER_ENV_FRAME.get(shape_key)
         peak = SM_COUNT * SMSP_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
         ach = per * w.n_envs * w.frameskip / dur / 1e9 if per else None
-        tb = INTERP_DRAM_BYTES_PER_ENV_STEP.get(args.form)
+        tb = INTERP_DRAM_BYTES_PER_ENV_STEP.get(shape_key)
         roof = {"bound": "alu", "kernel": "interpreter", "achieved": ach, "peak": peak, "unit": "Gwarp-inst/s",
                 "frac": (ach / peak) if ach else None, "traffic": tb * w.n_envs if tb else None,
                 "launch_ms": dur * 1000.0,
