@@ -251,10 +251,27 @@ def main():
     K, W = args.steps, args.warmup
     acts = torch.from_numpy(synth.actions(100 + rank, K + W, w.n_envs)).cuda()
     obs, rew, done = env.alloc_outputs()
+    inference = args.config == 5
+    if inference:
+        # inference-path loop: the policy picks every action on the device and
+        # each step appends the newest plane and reward to a 5-deep ring
+        weights = torch.from_numpy(synth.policy_weights(w.seed).view(np.int16)).cuda()
+        ring = torch.zeros((5, w.n_envs, 84 * 84), dtype=torch.uint8, device="cuda")
+        ring_r = torch.zeros((5, w.n_envs), dtype=torch.float32, device="cuda")
+        obs.zero_()
+        pol_act = torch.empty(w.n_envs, dtype=torch.uint8, device="cuda")
+        t_ring = [0]
+
+        def do_step(a):
+            env.rollout(weights, 1, obs, pol_act, rew, done, ring, ring_r, ring_start=t_ring[0])
+            t_ring[0] += 1
+    else:
+        def do_step(a):
+            env.step(a, obs, rew, done)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     for s in range(W):
-        env.step(acts[s], obs, rew, done)
+        do_step(acts[s])
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     instr = 0
@@ -267,7 +284,7 @@ def main():
     for s in range(K):
         flush.fill_(s & 0xFF)
         ev[s][0].record(stream)
-        env.step(acts[W + s], obs, rew, done)
+        do_step(acts[W + s])
         ev[s][1].record(stream)
         a, b = env.counters()
         instr += a
@@ -285,7 +302,7 @@ def main():
     env.profile(True)
     for s in range(prof_steps):
         flush.fill_(s & 0xFF)
-        env.step(pacts[s], obs, rew, done)
+        do_step(pacts[s])
     torch.cuda.synchronize()
     env.profile(False)
     prof = env.profile_read()
@@ -302,7 +319,7 @@ def main():
 
     # e2e through the host-buffer entry point (pinned host memory)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not inference:
         ha = torch.from_numpy(synth.actions(200 + rank, 8 + K, w.n_envs)).pin_memory()
         ho = torch.empty(env.obs_shape(), dtype=torch.uint8).pin_memory()
         hr = torch.empty(w.n_envs, dtype=torch.int32).pin_memory()
@@ -343,7 +360,8 @@ def main():
             "ms_per_step": 1000.0 * total_s_max / K, "p50_step_ms": p50, "p99_step_ms": p99,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic (seeded cartridges and actions)",
-            "config": {"workload": w.name, "n_envs": w.n_envs, "n_roms": len(w.roms), "frameskip": w.frameskip,
+            "config": {"workload": w.name + (" (policy + step + ring per step)" if inference else ""),
+                       "n_envs": w.n_envs, "n_roms": len(w.roms), "frameskip": w.frameskip,
                        "output": "84x84x4 uint8 stack" if w.output_mode == 1 else "210x160 palette frame",
                        "form": args.form, "l2": "flushed (256 MB write) before each timed step",
                        "launch_shape": dict(zip(["envs_per_warp", "envs_per_block", "warps_per_frame", "grid"],

@@ -135,6 +135,35 @@ ATARI_API int atari_env_step(atari_env *env, const uint8_t *d_actions, uint8_t *
 ATARI_API int atari_env_step_host(atari_env *env, const uint8_t *actions, uint8_t *obs, int32_t *rewards,
                         uint8_t *dones, atari_stream stream);
 
+/*
+ * Inference-path policy (paper Section 4, inference-only measurements: a
+ * network picks actions on the GPU next to the emulator).  A linear softmax
+ * over the stack: logits[j] = sum_k obs[k] * W[k][j] for k = plane * 7056 +
+ * row * 84 + column, d_weights (device) = bf16 bit patterns [28224][18],
+ * fp32 accumulation in a fixed order (441 chunks of 64 sequential fused
+ * multiply-adds; chunk partials reduced by s[i] += s[i + h], h = 256 .. 1,
+ * over 512 zero-padded slots), softmax weights exp(l - max) by Cody-Waite
+ * reduction and a degree-7 polynomial, action = smallest j whose running
+ * weight sum exceeds u * total, u = 24-bit fraction of the env's Philox word
+ * (seed; env key, step, 4 << 8, episode).  d_obs (device) = [n][4][84][84]
+ * (stack output mode required); d_actions (device, n) receives the actions,
+ * d_logits (device, n * 18 floats, may be NULL) the logits.
+ */
+ATARI_API int atari_env_policy(atari_env *env, const uint8_t *d_obs, const uint16_t *d_weights, uint8_t *d_actions,
+                               float *d_logits, atari_stream stream);
+
+/*
+ * The inference-path loop, entirely on the device: n_steps iterations of
+ * policy(d_obs) -> d_actions, atari_env_step(d_actions) -> d_obs, d_rewards,
+ * d_dones, then the newest plane of every env's stack and its reward (as
+ * float) appended to ring slot (ring_start + t) mod ring_depth of
+ * d_ring_planes (device, [ring_depth][n][84*84]) and d_ring_rewards
+ * (device, [ring_depth][n]).  No host synchronisation.
+ */
+ATARI_API int atari_env_rollout(atari_env *env, const uint16_t *d_weights, int n_steps, uint8_t *d_obs,
+                                uint8_t *d_actions, int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes,
+                                float *d_ring_rewards, int ring_depth, int ring_start, atari_stream stream);
+
 /* d_status (device, uint32 [n]) <- per-env status bits. */
 ATARI_API int atari_env_status(atari_env *env, uint32_t *d_status, atari_stream stream);
 
@@ -187,7 +216,8 @@ ATARI_API int atari_env_counters(atari_env *env, uint64_t *instructions, uint64_
 #define ATARI_PROF_RASTER 1     /* TIA replay into frames */
 #define ATARI_PROF_PREPROC 2    /* luma / max / 84x84 / stack */
 #define ATARI_PROF_FUSED 3      /* fused replay + preprocessing (batched form) */
-#define ATARI_PROF_COPY 4       /* output copies */
+#define ATARI_PROF_COPY 4       /* output copies, rollout-ring appends */
+#define ATARI_PROF_POLICY 5     /* linear softmax policy */
 ATARI_API int atari_env_profile(atari_env *env, int enable);
 ATARI_API int atari_env_profile_read(atari_env *env, double *ms, uint64_t *launches);
 

@@ -54,8 +54,18 @@
  *       tier a playfield pixel is chosen before a ball pixel.
  *   INPT4 reads 0x00 while fire is pressed; with VBLANK D6 set, a press is
  *       latched until a VBLANK write clears D6.
+ *   Policy (inference-path loop, Section 4's inference-only measurements with
+ *       a DNN picking actions on the device): a linear softmax over the
+ *       84x84x4 stack with bf16 weights and fp32 accumulation; the fp32
+ *       reduction order is fixed (441 chunks of 64 sequential fmaf, partials
+ *       reduced pairwise s[i] += s[i + h] for h = 256, 128, ..., 1 over 512
+ *       zero-padded slots), exp is Cody-Waite reduction plus a degree-7
+ *       Taylor polynomial, and the action is the smallest j whose running
+ *       sum exceeds u * total, u = (x >> 8) 2^-24 for the env's Philox word
+ *       x (the last action with nonzero weight if rounding leaves none).
  */
 #include "oracle.h"
+#include <math.h>
 #include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
@@ -896,6 +906,7 @@ static uint32_t mulhi(uint32_t x, uint32_t n) { return (uint32_t)(((uint64_t)x *
 #define PURPOSE_STICKY 1u
 #define PURPOSE_RESET 2u
 #define PURPOSE_CACHE 3u
+#define PURPOSE_POLICY 4u
 
 /* ------------------------------------------------------------------ preprocessing */
 
@@ -1172,4 +1183,110 @@ uint64_t orc_envs_instructions(const orc_envs *e) {
     uint64_t s = 0;
     for (int i = 0; i < e->n_envs; i++) s += e->env[i].instret;
     return s;
+}
+
+/* ------------------------------------------------------------------ policy */
+
+/* exp(x) for x <= 0 (and small positive x): x = k ln2 + r with the two-part
+ * Cody-Waite constant (C1 = 355/512 exactly representable, C2 the
+ * remainder), exp(r) by the degree-7 Taylor polynomial in Horner form with
+ * fused multiply-adds, scaled by 2^k through the exponent field.  Results
+ * below the normal range are flushed to 0. */
+float orc_exp_own(float x) {
+    if (x < -87.0f) return 0.0f;
+    float kf = rintf(x * 1.44269504088896341f);
+    float r = fmaf(-kf, 0.693359375f, x);
+    r = fmaf(-kf, -2.12194440e-4f, r);
+    float p = 1.0f / 5040.0f;
+    p = fmaf(p, r, 1.0f / 720.0f);
+    p = fmaf(p, r, 1.0f / 120.0f);
+    p = fmaf(p, r, 1.0f / 24.0f);
+    p = fmaf(p, r, 1.0f / 6.0f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    int k = (int)kf;
+    if (k < -126) return 0.0f;
+    union { uint32_t u; float f; } sc;
+    sc.u = (uint32_t)(k + 127) << 23;
+    return p * sc.f;
+}
+
+static float bf16_to_f32(uint16_t b) {
+    union { uint32_t u; float f; } v;
+    v.u = (uint32_t)b << 16;
+    return v.f;
+}
+
+void orc_policy_logits(const uint8_t *x, const uint16_t *w, float *logits) {
+    static __thread float part[512][ORC_POLICY_A];
+    for (int c = 0; c < 512; c++) {
+        for (int j = 0; j < ORC_POLICY_A; j++) part[c][j] = 0.0f;
+        if (c >= ORC_POLICY_K / 64) continue;
+        for (int q = 0; q < 64; q++) {
+            int k = c * 64 + q;
+            float xv = (float)x[k];
+            for (int j = 0; j < ORC_POLICY_A; j++)
+                part[c][j] = fmaf(xv, bf16_to_f32(w[(size_t)k * ORC_POLICY_A + j]), part[c][j]);
+        }
+    }
+    for (int h = 256; h >= 1; h >>= 1)
+        for (int i = 0; i < h; i++)
+            for (int j = 0; j < ORC_POLICY_A; j++) part[i][j] = part[i][j] + part[i + h][j];
+    for (int j = 0; j < ORC_POLICY_A; j++) logits[j] = part[0][j];
+}
+
+int orc_policy_sample(const float *l, uint32_t u) {
+    float m = l[0];
+    for (int j = 1; j < ORC_POLICY_A; j++) if (l[j] > m) m = l[j];
+    float e[ORC_POLICY_A], tot = 0.0f;
+    for (int j = 0; j < ORC_POLICY_A; j++) { e[j] = orc_exp_own(l[j] - m); tot = tot + e[j]; }
+    /* u as an exact 24-bit fraction in [0, 1); when rounding leaves every
+     * running sum at or below the threshold, the last action with nonzero
+     * weight is taken */
+    float thr = ((float)(u >> 8) * 5.9604644775390625e-08f) * tot;
+    float c = 0.0f;
+    int last = 0;
+    for (int j = 0; j < ORC_POLICY_A; j++) {
+        c = c + e[j];
+        if (e[j] > 0.0f) last = j;
+        if (c > thr) return j;
+    }
+    return last;
+}
+
+typedef struct {
+    const orc_envs *e;
+    const uint8_t *obs;
+    const uint16_t *w;
+    uint8_t *act;
+    float *logits;
+    int lo, hi;
+} policy_job;
+
+static void *policy_worker(void *p) {
+    policy_job *j = (policy_job *)p;
+    for (int i = j->lo; i < j->hi; i++) {
+        const orc_env *v = &j->e->env[i];
+        float l[ORC_POLICY_A];
+        orc_policy_logits(j->obs + (size_t)i * ORC_POLICY_K, j->w, l);
+        uint32_t u = philox_word(j->e->cfg.seed, v->env_key, v->step_no, PURPOSE_POLICY << 8, v->episode);
+        j->act[i] = (uint8_t)orc_policy_sample(l, u);
+        if (j->logits) memcpy(j->logits + (size_t)i * ORC_POLICY_A, l, sizeof l);
+    }
+    return NULL;
+}
+
+void orc_envs_policy(const orc_envs *e, const uint8_t *obs, const uint16_t *w, uint8_t *actions, float *logits,
+                     int n_threads) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > 64) n_threads = 64;
+    if (n_threads > e->n_envs) n_threads = e->n_envs ? e->n_envs : 1;
+    policy_job jobs[64];
+    pthread_t th[64];
+    for (int t = 0; t < n_threads; t++)
+        jobs[t] = (policy_job){e, obs, w, actions, logits, (int)((int64_t)e->n_envs * t / n_threads),
+                               (int)((int64_t)e->n_envs * (t + 1) / n_threads)};
+    for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, policy_worker, &jobs[t]);
+    for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
 }

@@ -90,6 +90,23 @@ void orc_envs_get_cache(const orc_envs *e, uint8_t *out /* n_roms*n_cache*256 */
 void orc_envs_reset(orc_envs *e, const uint8_t *mask /* NULL: all */);
 uint64_t orc_envs_instructions(const orc_envs *e); /* 6502 instructions retired (all envs) */
 
+/* ---- inference-path policy (linear softmax on the 84x84x4 stack) ---- */
+#define ORC_POLICY_K 28224
+#define ORC_POLICY_A 18
+/* exp by Cody-Waite range reduction and a degree-7 polynomial, fp32, fmaf */
+float orc_exp_own(float x);
+/* logits of one stack: canonical order (441 chunks of 64 sequential fmaf,
+ * chunk partials reduced by a strided-halving tree over 512 slots) */
+void orc_policy_logits(const uint8_t *stack, const uint16_t *w_bf16, float *logits18);
+/* action from logits and a 32-bit uniform word x: smallest j with
+ * cumsum(exp_own(l - max)) > ((x >> 8) 2^-24) * sum, else the last j with
+ * nonzero weight */
+int orc_policy_sample(const float *logits18, uint32_t u);
+/* for every env: logits from obs (n x 28224), draw from the env's Philox
+ * stream (env key, step, 4 << 8, episode), action out */
+void orc_envs_policy(const orc_envs *e, const uint8_t *obs, const uint16_t *w_bf16, uint8_t *actions,
+                     float *logits, int n_threads);
+
 /* ---- preprocessing of one env-step (exposed for the downsample pins) ---- */
 void orc_preprocess(const uint8_t *f3, const uint8_t *f4, const uint8_t *luma128,
                     uint8_t *out84x84);

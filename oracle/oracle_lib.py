@@ -25,7 +25,8 @@ def build(force: bool = False) -> str:
              os.path.getmtime(os.path.join(HERE, "oracle.h"))))
     if force or stale:
         tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, SRC, "-lpthread"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC,
+                               "-lpthread", "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -74,6 +75,11 @@ def lib():
             L.orc_envs_instructions.restype = C.c_uint64
             L.orc_envs_instructions.argtypes = [P]
             L.orc_preprocess.argtypes = [P, P, P, P]
+            L.orc_exp_own.argtypes = [C.c_float]
+            L.orc_exp_own.restype = C.c_float
+            L.orc_policy_logits.argtypes = [P, P, P]
+            L.orc_policy_sample.argtypes = [P, C.c_uint32]
+            L.orc_envs_policy.argtypes = [P, P, P, P, P, C.c_int]
             _lib = L
     return _lib
 
@@ -100,6 +106,23 @@ def philox4x32_10(ctr, key):
     o = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
     return [int(v) for v in o]
+
+
+def exp_own(x: float) -> float:
+    return lib().orc_exp_own(x)
+
+
+def policy_logits(stack: np.ndarray, w_bf16: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(stack, dtype=np.uint8).reshape(-1)
+    w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    out = np.zeros(18, dtype=np.float32)
+    lib().orc_policy_logits(_ptr(x), _ptr(w), _ptr(out))
+    return out
+
+
+def policy_sample(logits: np.ndarray, u: int) -> int:
+    l = np.ascontiguousarray(logits, dtype=np.float32)
+    return lib().orc_policy_sample(_ptr(l), u)
 
 
 def preprocess(f3: np.ndarray, f4: np.ndarray, luma: bytes) -> np.ndarray:
@@ -222,6 +245,15 @@ class OracleEnvs:
     def reset(self, mask=None):
         m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
         lib().orc_envs_reset(self.h, _ptr(m) if m is not None else None)
+
+    def policy(self, obs, w_bf16, n_threads: int = 1):
+        """Actions (and logits) of the linear softmax policy for every env."""
+        o = np.ascontiguousarray(obs, dtype=np.uint8)
+        w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+        act = np.zeros(self.n_envs, dtype=np.uint8)
+        logits = np.zeros((self.n_envs, 18), dtype=np.float32)
+        lib().orc_envs_policy(self.h, _ptr(o), _ptr(w), _ptr(act), _ptr(logits), n_threads)
+        return act, logits
 
     def instructions(self) -> int:
         return lib().orc_envs_instructions(self.h)

@@ -20,6 +20,7 @@
 #include "device_machine.cuh"
 #include "render.cuh"
 #include "batched.cuh"
+#include "policy.cuh"
 
 using namespace atari;
 
@@ -1136,6 +1137,46 @@ int atari_env_counters(atari_env *E, uint64_t *instructions, uint64_t *log_recor
   for (int i = 0; i < E->n; ++i) { a += h[2 * i]; b += h[2 * i + 1]; }
   if (instructions) *instructions = a;
   if (log_records) *log_records = b;
+  return 0;
+}
+
+int atari_env_policy(atari_env *E, const uint8_t *d_obs, const uint16_t *d_weights, uint8_t *d_actions,
+                     float *d_logits, atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->cfg.output_mode != ATARI_OUT_STACK) return fail(ATARI_EINVAL, "the policy reads the 84x84x4 stack output");
+  if (E->n == 0) return 0;
+  if (!d_obs || !d_weights || !d_actions) return fail(ATARI_EINVAL, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    ProfScope p(E, ATARI_PROF_POLICY, s);
+    k_policy<<<E->n, 512, 0, s>>>(d_obs, d_weights, E->d_state, d_actions, d_logits, E->n, E->cfg.seed);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int atari_env_rollout(atari_env *E, const uint16_t *d_weights, int n_steps, uint8_t *d_obs, uint8_t *d_actions,
+                      int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes, float *d_ring_rewards,
+                      int ring_depth, int ring_start, atari_stream stream) {
+  g_err.clear();
+  if (!E) return fail(ATARI_EINVAL, "env is NULL");
+  if (E->cfg.output_mode != ATARI_OUT_STACK) return fail(ATARI_EINVAL, "the rollout loop needs stack output");
+  if (n_steps < 0 || ring_depth < 1 || ring_start < 0) return fail(ATARI_EINVAL, "bad n_steps / ring arguments");
+  if (E->n == 0 || n_steps == 0) return 0;
+  if (!d_weights || !d_obs || !d_actions || !d_rewards || !d_dones || !d_ring_planes || !d_ring_rewards)
+    return fail(ATARI_EINVAL, "NULL buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int t = 0; t < n_steps; ++t) {
+    if (int rc = atari_env_policy(E, d_obs, d_weights, d_actions, nullptr, stream)) return rc;
+    if (int rc = atari_env_step(E, d_actions, d_obs, d_rewards, d_dones, stream)) return rc;
+    {
+      ProfScope p(E, ATARI_PROF_COPY, s);
+      k_ring_append<<<E->n, 128, 0, s>>>(d_obs, d_rewards, d_ring_planes, d_ring_rewards, E->n,
+                                        (ring_start + t) % ring_depth);
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
   return 0;
 }
 

@@ -101,6 +101,9 @@ __device__ __noinline__ uint32_t fc_riot_read(uint32_t addr, uint64_t now, uint3
 }
 
 // ---------------------------------------------------------------- the console
+struct FastConsole;
+__device__ __forceinline__ void fc_exec_general(FastConsole *self);
+
 struct FastConsole {
   // shared-memory views
   const uint32_t *romw;    // staged cartridge words (banks of 4096)
@@ -448,8 +451,197 @@ struct FastConsole {
     fn = fz = (reg - v) & 0xFF;
   }
 
-  // ---- one instruction ----
-  __device__ __forceinline__ void exec() {
+
+  // ---- single bus sites of the hot path ----
+  __device__ __forceinline__ uint32_t bus_read(uint32_t ea, uint32_t t) {
+    const uint32_t a = ea & 0x1FFF;
+    if ((a & 0x1280) == 0x0080) return ram[(a & 0x7F) * E];
+    if (a & 0x1000) {
+      const uint32_t off = a & 0xFFF;
+      if (scheme) hotspot(off);
+      return romw[bank * 4096u + off] & 0xFF;
+    }
+    if (!(a & 0x80)) return tia_read(a & 0x0F, t);
+    return fc_riot_read(a, 76ull * L0 + t, ports, joy, tim_cw, tim_v, tim_shift);
+  }
+  __device__ __forceinline__ void bus_write(uint32_t ea, uint32_t v, uint32_t t) {
+    const uint32_t a = ea & 0x1FFF;
+    if ((a & 0x1280) == 0x0080) { ram[(a & 0x7F) * E] = v & 0xFF; return; }
+    if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
+    if (!(a & 0x80)) { tia_write(a & 0x3F, v & 0xFF, t); return; }
+    riot_write(a, v, t);
+  }
+
+  // ---- one instruction, hot form ----
+  // Handles every instruction whose fetch comes from the cartridge away from
+  // hotspots, except BRK, RTI, JMP (ind), stack accesses outside RAM and
+  // indirect pointers outside RAM; those run exec_general out of line on a
+  // copy of the register state.  One bus-read and one bus-write site.
+  __device__ __forceinline__ bool exec() {
+    const uint32_t k0 = kf;
+    const uint32_t pc = PC;
+    const uint32_t off = pc & 0xFFF;
+    if (!(pc & 0x1000) || off > (scheme ? 0xFF3u : 0xFFDu)) return false;
+    const uint32_t w = romw[bank * 4096u + off];
+    const uint32_t op = dec_op[w & 0xFF];
+    const uint32_t mode = romw_mode(w);
+    uint32_t n = romw_cycles(w);
+    const uint32_t b1 = (w >> 8) & 0xFF, b2 = (w >> 16) & 0xFF;
+    if (op == O_JAM || op == O_BRK || op == O_RTI || mode == IND) return false;
+    uint32_t ea = 0, cross = 0, len = 2;
+    switch (mode) {
+      case IMP: case ACC: len = 1; break;
+      case IMM: break;
+      case ZP: ea = b1; break;
+      case ZPX: ea = (b1 + X) & 0xFF; break;
+      case ZPY: ea = (b1 + Y) & 0xFF; break;
+      case ABS: ea = b1 | b2 << 8; len = 3; break;
+      case ABX: { uint32_t b = b1 | b2 << 8; ea = (b + X) & 0xFFFF; cross = (b ^ ea) >> 8; len = 3; break; }
+      case ABY: { uint32_t b = b1 | b2 << 8; ea = (b + Y) & 0xFFFF; cross = (b ^ ea) >> 8; len = 3; break; }
+      case IZX: {
+        const uint32_t z = (b1 + X) & 0xFF;
+        if (!(z & 0x80) || z == 0xFF) return false;            // pointer bytes outside RAM
+        ea = ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8;
+        break;
+      }
+      case IZY: {
+        if (!(b1 & 0x80) || b1 == 0xFF) return false;
+        const uint32_t b = ram[(b1 & 0x7F) * E] | ram[((b1 + 1) & 0x7F) * E] << 8;
+        ea = (b + Y) & 0xFFFF;
+        cross = (b ^ ea) >> 8;
+        break;
+      }
+      default: break;  // REL
+    }
+    const uint32_t next = (pc + len) & 0xFFFF;
+    if (cross && (w >> 31)) n++;
+    if (mode == REL) {
+      uint32_t take;
+      switch (op) {
+        case O_BCC: take = fc ^ 1u; break;
+        case O_BCS: take = fc; break;
+        case O_BNE: take = (fz & 0xFF) ? 1u : 0u; break;
+        case O_BEQ: take = (fz & 0xFF) ? 0u : 1u; break;
+        case O_BVC: take = fv ? 0u : 1u; break;
+        case O_BVS: take = fv ? 1u : 0u; break;
+        case O_BPL: take = (fn & 0x80) ? 0u : 1u; break;
+        default: take = (fn & 0x80) ? 1u : 0u; break;
+      }
+      PC = next;
+      if (take) {
+        const uint32_t tgt = (next + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF;
+        n += ((next ^ tgt) & 0xFF00) ? 2u : 1u;
+        PC = tgt;
+      }
+      kf = k0 + n;
+      instret++;
+      return true;
+    }
+    // stack and flow: RAM stack only
+    switch (op) {
+      case O_PHA: case O_PHP:
+        if (!(SP & 0x80)) return false;
+        ram[(SP & 0x7F) * E] = op == O_PHA ? A : (P() | 0x10u);
+        SP = (SP - 1) & 0xFF;
+        PC = next; kf = k0 + n; instret++;
+        return true;
+      case O_PLA: case O_PLP: {
+        const uint32_t sp1 = (SP + 1) & 0xFF;
+        if (!(sp1 & 0x80)) return false;
+        SP = sp1;
+        const uint32_t v = ram[(sp1 & 0x7F) * E];
+        if (op == O_PLA) { A = v; fn = fz = v; } else setP(v);
+        PC = next; kf = k0 + n; instret++;
+        return true;
+      }
+      case O_JSR: {
+        if (SP < 0x81) return false;
+        const uint32_t ret = (pc + 2) & 0xFFFF;
+        ram[(SP & 0x7F) * E] = ret >> 8;
+        ram[((SP - 1) & 0x7F) * E] = ret & 0xFF;
+        SP = (SP - 2) & 0xFF;
+        PC = ea; kf = k0 + n; instret++;
+        return true;
+      }
+      case O_RTS: {
+        const uint32_t s1 = (SP + 1) & 0xFF, s2 = (SP + 2) & 0xFF;
+        if (!(s1 & 0x80) || !(s2 & 0x80)) return false;
+        const uint32_t lo = ram[(s1 & 0x7F) * E], hi = ram[(s2 & 0x7F) * E];
+        SP = s2;
+        PC = ((lo | hi << 8) + 1) & 0xFFFF; kf = k0 + n; instret++;
+        return true;
+      }
+      case O_JMP: PC = ea; kf = k0 + n; instret++; return true;
+      default: break;
+    }
+    const uint32_t kA = k0 + n - 1;
+    const bool rmw = op == O_ASL || op == O_LSR || op == O_ROL || op == O_ROR || op == O_INC || op == O_DEC;
+    const bool store = op == O_STA || op == O_STX || op == O_STY;
+    wsync = 0;
+    vs_rise = 0;
+    // the single read site: operand of read instructions and read-modify-write
+    uint32_t v = 0;
+    if (mode == IMM) v = b1;
+    else if (mode == ACC) v = A;
+    else if (!store && mode != IMP) v = bus_read(ea, rmw ? kA - 2 : kA);
+    uint32_t r = v;
+    switch (op) {
+      case O_LDA: A = v; fn = fz = v; break;
+      case O_LDX: X = v; fn = fz = v; break;
+      case O_LDY: Y = v; fn = fz = v; break;
+      case O_STA: r = A; break;
+      case O_STX: r = X; break;
+      case O_STY: r = Y; break;
+      case O_ADC: adc(v); break;
+      case O_SBC: sbc(v); break;
+      case O_AND: A &= v; fn = fz = A; break;
+      case O_ORA: A |= v; fn = fz = A; break;
+      case O_EOR: A ^= v; fn = fz = A; break;
+      case O_CMP: cmp(A, v); break;
+      case O_CPX: cmp(X, v); break;
+      case O_CPY: cmp(Y, v); break;
+      case O_BIT: fn = v; fv = v & 0x40; fz = A & v; break;
+      case O_ASL: r = (v << 1) & 0xFF; fc = v >> 7; fn = fz = r; break;
+      case O_LSR: r = v >> 1; fc = v & 1; fn = fz = r; break;
+      case O_ROL: r = ((v << 1) | fc) & 0xFF; fc = v >> 7; fn = fz = r; break;
+      case O_ROR: r = (v >> 1) | (fc << 7); fc = v & 1; fn = fz = r; break;
+      case O_INC: r = (v + 1) & 0xFF; fn = fz = r; break;
+      case O_DEC: r = (v - 1) & 0xFF; fn = fz = r; break;
+      case O_INX: X = (X + 1) & 0xFF; fn = fz = X; break;
+      case O_INY: Y = (Y + 1) & 0xFF; fn = fz = Y; break;
+      case O_DEX: X = (X - 1) & 0xFF; fn = fz = X; break;
+      case O_DEY: Y = (Y - 1) & 0xFF; fn = fz = Y; break;
+      case O_TAX: X = A; fn = fz = X; break;
+      case O_TAY: Y = A; fn = fz = Y; break;
+      case O_TXA: A = X; fn = fz = A; break;
+      case O_TYA: A = Y; fn = fz = A; break;
+      case O_TSX: X = SP; fn = fz = X; break;
+      case O_TXS: SP = X; break;
+      case O_CLC: fc = 0; break;
+      case O_SEC: fc = 1; break;
+      case O_CLI: fdi &= ~0x04u; break;
+      case O_SEI: fdi |= 0x04u; break;
+      case O_CLV: fv = 0; break;
+      case O_CLD: fdi &= ~0x08u; break;
+      case O_SED: fdi |= 0x08u; break;
+      default: break;  // NOP
+    }
+    if (rmw && mode == ACC) A = r;
+    // the single write site: stores, and the two writes of read-modify-write
+    if (store || (rmw && mode != ACC)) {
+#pragma unroll 1
+      for (uint32_t wi = store ? 1u : 0u; wi < 2; ++wi) bus_write(ea, wi ? r : v, kA - 1 + wi);
+    }
+    PC = next;
+    uint32_t k = k0 + n;
+    if (wsync) k = ((k + 75u) / 76u) * 76u;
+    kf = k;
+    instret++;
+    return true;
+  }
+
+  // ---- one instruction, general form (every case; used out of line) ----
+  __device__ __forceinline__ void exec_general() {
     const uint32_t k0 = kf;
     wsync = 0;
     vs_rise = 0;
@@ -589,9 +781,10 @@ struct FastConsole {
 
   __device__ __forceinline__ uint32_t run_frame() {
     uint32_t next_rel;
+    vs_rise = 0;
     for (;;) {
       if (jam) { next_rel = kf / 76u; break; }
-      exec();
+      if (!exec()) fc_exec_general(this);
       if (jam) { next_rel = kf / 76u; break; }
       if (vs_rise) { next_rel = vs_kf / 76u; break; }
       if (kf >= 76u * CAP_LINES) { status |= ST_FRAME_CAP; next_rel = kf / 76u; break; }
@@ -604,5 +797,14 @@ struct FastConsole {
     return next_rel;
   }
 };
+
+// Out-of-line general instruction: runs on a copy of the register state (the
+// caller's console stays in registers; only this rare path touches memory).
+__device__ __noinline__ void fc_exec_general_impl(FastConsole *c) { c->exec_general(); }
+__device__ __forceinline__ void fc_exec_general(FastConsole *self) {
+  FastConsole tmp = *self;
+  fc_exec_general_impl(&tmp);
+  *self = tmp;
+}
 
 }  // namespace atari

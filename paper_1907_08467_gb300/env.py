@@ -38,9 +38,10 @@ EXPORTS = ["atari_default_config", "atari_env_create", "atari_env_reset", "atari
            "atari_env_step_host", "atari_env_status", "atari_env_get_state", "atari_env_set_state",
            "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
            "atari_env_footprint", "atari_env_destroy", "atari_last_error", "atari_env_profile",
-           "atari_env_profile_read", "atari_env_launch_shape", "atari_step_noalloc"]
+           "atari_env_profile_read", "atari_env_launch_shape", "atari_step_noalloc", "atari_env_policy",
+           "atari_env_rollout"]
 PROF_SLOTS = 8
-PROF_NAMES = ["interpreter", "rasteriser", "preprocess", "fused_raster_preprocess", "copy", "s5", "s6", "s7"]
+PROF_NAMES = ["interpreter", "rasteriser", "preprocess", "fused_raster_preprocess", "copy", "policy", "s6", "s7"]
 
 
 def load_library(path: str | None = None):
@@ -75,10 +76,13 @@ def load_library(path: str | None = None):
         L.atari_step_noalloc.argtypes = [P, C.c_size_t, _Meta, P, P, C.c_int, P, P, P, P, C.c_int, C.c_int,
                                          C.c_int, C.c_uint64, P]
         L.atari_step_noalloc.restype = C.c_int
+        L.atari_env_policy.argtypes = [P, P, P, P, P, P]
+        L.atari_env_rollout.argtypes = [P, P, C.c_int, P, P, P, P, P, P, C.c_int, C.c_int, P]
         for name in ("atari_env_create", "atari_env_reset", "atari_env_step", "atari_env_step_host",
                      "atari_env_status", "atari_env_get_state", "atari_env_set_state",
                      "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
-                     "atari_env_profile", "atari_env_profile_read", "atari_env_launch_shape"):
+                     "atari_env_profile", "atari_env_profile_read", "atari_env_launch_shape",
+                     "atari_env_policy", "atari_env_rollout"):
             getattr(L, name).restype = C.c_int
         if path is None:
             _lib = L
@@ -251,6 +255,22 @@ class AtariEnv:
         ln = (C.c_uint64 * PROF_SLOTS)()
         _check(self.lib.atari_env_profile_read(self.h, ms, ln))
         return {PROF_NAMES[k]: (ms[k], ln[k]) for k in range(PROF_SLOTS) if ln[k]}
+
+    def policy(self, obs, weights, actions=None, logits=None, stream=None):
+        """Linear softmax policy on the stack (see atari_env_policy); returns actions."""
+        t = self._torch
+        if actions is None:
+            actions = t.empty(self.n, dtype=t.uint8, device=self.device)
+        _check(self.lib.atari_env_policy(self.h, _ptr(obs), _ptr(weights), _ptr(actions), _ptr(logits),
+                                         _stream(stream)))
+        return actions
+
+    def rollout(self, weights, n_steps, obs, actions, rewards, dones, ring_planes, ring_rewards, ring_start=0,
+                stream=None):
+        """n_steps of policy -> step -> ring append, all on the device."""
+        _check(self.lib.atari_env_rollout(self.h, _ptr(weights), n_steps, _ptr(obs), _ptr(actions), _ptr(rewards),
+                                          _ptr(dones), _ptr(ring_planes), _ptr(ring_rewards),
+                                          ring_planes.shape[0], ring_start, _stream(stream)))
 
     def launch_shape(self):
         """(envs per warp, envs per block, warps per frame, interpreter grid)."""

@@ -5,3 +5,4 @@ from .asm6502 import assemble, Assembler, OPCODES, SYMBOLS  # noqa: F401
 from .roms import (Rom, Workload, workload, actions, luma_table, rom_playfield,  # noqa: F401
                    rom_sprite, rom_banked)
 from .fuzz import fuzz_rom  # noqa: F401,E402
+from .policy import policy_weights  # noqa: F401,E402
