@@ -540,7 +540,7 @@ int build_groups(atari_env *E, int lanes, int warps) {
   E->n_groups = ng;
   E->lanes = lanes;
   E->warps = warps;
-  size_t smem = (size_t)E->romw_words * 4 + 512 + (size_t)lanes * warps * (512 + TIA_BYTES);
+  size_t smem = (size_t)E->romw_words * 4 + 512 + (size_t)lanes * warps * (512 + 4 * IO_WORDS + TIA_BYTES);
   int per_sm = 0;
   CUDA_TRY(cudaFuncSetAttribute(k_interp_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched, warps * 32, smem));
@@ -589,7 +589,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
 }
 
 size_t interp_smem(const atari_env *E) {
-  return (size_t)E->romw_words * 4 + 512 + (size_t)E->lanes * E->warps * (512 + TIA_BYTES);
+  return (size_t)E->romw_words * 4 + 512 + (size_t)E->lanes * E->warps * (512 + 4 * IO_WORDS + TIA_BYTES);
 }
 size_t fused_smem() { return 2 * 210 * 160 + 128 + 7056; }
 
@@ -944,7 +944,8 @@ int autotune(atari_env *E) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cand[][2] = {{32, 4}, {32, 2}, {32, 1}, {16, 4}, {16, 2}, {8, 4}, {8, 2}, {4, 4}, {2, 4}, {1, 4}};
+  const int cand[][2] = {{32, 4}, {32, 2}, {32, 1}, {16, 4}, {16, 2}, {16, 1}, {8, 4}, {8, 2}, {8, 1},
+                         {4, 4}, {4, 2}, {4, 1}, {2, 4}, {2, 2}, {1, 4}};
   float best = 1e30f;
   int bl = 32, bw = 4;
   bool was_prof = E->profiling;

@@ -83,24 +83,23 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
     const bool logging = slot >= a.first_slot;
     if (logging) {
       m.snapshot(a.snap + ((size_t)i * 2 + slot) * 64);
-      m.logp = a.log + ((size_t)i * 2 + slot) * a.log_cap;
-      m.logn = 0;
-      m.logcap = (uint32_t)a.log_cap;
+      m.set_log(a.log + ((size_t)i * 2 + slot) * a.log_cap, (uint32_t)a.log_cap);
     } else {
-      m.logp = nullptr;
+      m.set_log(nullptr, 0);
     }
     const uint32_t lines = m.run_frame();
     if (logging) {
       uint32_t *mt = a.meta + ((size_t)i * 2 + slot) * 2;
-      mt[0] = m.logn;
+      const uint32_t nrec = m.log_count();
+      mt[0] = nrec;
       mt[1] = lines;
-      log_total += m.logn;
+      log_total += nrec;
     }
     const uint32_t s = m.ram[score * m.E];
     reward += (int32_t)(int8_t)(uint8_t)(s - score_prev);
     score_prev = s;
   }
-  env_status |= m.status;
+  env_status |= m.all_status();
   if (m.jam) env_status |= ST_ILLEGAL;
   const uint32_t done = (m.ram[gameover * m.E] != 0 || m.jam) ? 1u : 0u;
   a.rew_int[i] = reward;
@@ -128,7 +127,8 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
   uint32_t *romw = reinterpret_cast<uint32_t *>(smem);
   uint8_t *dec_op = smem + (size_t)a.romw_words * 4;
   uint32_t *ram = reinterpret_cast<uint32_t *>(dec_op + 512);
-  uint8_t *tia = reinterpret_cast<uint8_t *>(ram + 128 * a.E);
+  uint32_t *iow = ram + 128 * a.E;
+  uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_WORDS * a.E);
   __shared__ int s_group;
   for (int t = threadIdx.x; t < 512; t += blockDim.x) dec_op[t] = a.dec_op[t];
   int cur_rom = -1;
@@ -148,9 +148,12 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
       cur_rom = rom;
       __syncthreads();
     }
-    if (lane < a.lanes) {
-      const int j = warp * a.lanes + lane;
-      if (j < a.grp_count[g]) {
+    const int jj = warp * a.lanes + lane;
+    const bool runs = lane < a.lanes && jj < a.grp_count[g];
+    const uint32_t wmask = __ballot_sync(0xFFFFFFFFu, runs);
+    if (runs) {
+      const int j = jj;
+      {
         const int i = a.perm[a.grp_start[g] + j];
         uint8_t *st = a.state + (size_t)i * 256;
         const uint32_t inf = a.info[rom];
@@ -158,9 +161,10 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
         m.romw = romw;
         m.dec_op = dec_op;
         m.ram = ram + j;
-        m.tia = tia + j;
+        m.io = IoCtx{tia + j, iow + j, (uint32_t)a.E};
         m.E = (uint32_t)a.E;
         m.scheme = inf & 0xFF;
+        m.wmask = wmask;
         m.load(st);
         fast_step_env(m, st, i, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
       }

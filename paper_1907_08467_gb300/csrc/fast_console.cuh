@@ -1,18 +1,22 @@
-// Register-resident console for the batched form.
+// Console for the batched form, laid out for the issue rate of sm_103a.
 //
-// Same machine and the same canonical state as Console in
-// device_machine.cuh, laid out for speed on sm_103a:
-//   - CPU registers, split flags (N and Z kept as the last result byte),
-//     cycle counter, RIOT state and the collision-liveness shadows of the
-//     TIA in registers;
+// Same machine and canonical state as Console in device_machine.cuh:
+//   - the hot loop is a single switch on the opcode byte; every case has its
+//     addressing mode and cycle count folded in, so an emulated instruction
+//     costs one shared-memory fetch, one indirect branch and its own work;
+//   - CPU registers (flags split, N and Z kept as the last result byte),
+//     the cycle counter and the bank in registers;
 //   - RAM in shared memory, one 32-bit word per byte, interleaved by env
-//     (word = addr * E + env) so a warp's RAM accesses never bank-conflict;
-//   - the 37-byte TIA register file in shared memory (byte per register,
-//     interleaved the same way), read only on cold paths;
+//     (word = address * E + env): a warp's RAM accesses never bank-conflict;
+//   - the TIA register file (bytes) and the I/O state (collision cursor and
+//     latches, RIOT timer and ports, inputs, log cursor, frame base line)
+//     in shared memory, interleaved the same way, touched only by the
+//     out-of-line I/O functions below;
 //   - the block's cartridge staged in shared memory as one word per byte
-//     offset: bytes off, off+1, off+2 and the addressing mode / cycle count
-//     of the opcode at off, so an instruction is fetched with one load.
-// Collision-mask evaluation and RIOT/TIA reads are out of line (cold paths).
+//     offset (bytes off .. off+3), so an instruction is fetched with one load.
+// Instructions the hot switch does not take (BRK, RTI, JMP (ind), undocumented
+// opcodes, stack or pointer bytes outside RAM, fetches outside the cartridge
+// or next to a bank hotspot) run the general decoder out of line.
 #pragma once
 #include <cstdint>
 
@@ -27,49 +31,87 @@ enum TiaSlot : uint32_t {
   T_GRP1_O, T_VDELP0, T_VDELP1, T_VDELBL, T_RESMP0, T_RESMP1, T_HMP0, T_HMP1, T_HMM0, T_HMM1, T_HMBL,
   T_P0, T_P1, T_M0, T_M1, T_BL
 };
+// I/O state words (shared memory, interleaved by env)
+enum IoWord : uint32_t {
+  IO_CEVAL = 0, IO_CX, IO_L0LO, IO_L0HI, IO_BARLO, IO_BARHI, IO_TCWLO, IO_TCWHI, IO_TV, IO_TSH, IO_PORTS,
+  IO_JOY, IO_FIRE, IO_LATCH, IO_LOGLO, IO_LOGHI, IO_LOGN, IO_LOGCAP, IO_STATUS, IO_WORDS
+};
+constexpr uint32_t IO_WSYNC = 1u, IO_VSYNC_RISE = 2u;
 
-// Staged-ROM word: byte0 | byte1 << 8 | byte2 << 16 | mode << 24 | cycles << 28 (bit 31: penalty)
 __host__ __device__ constexpr uint32_t romw_mode(uint32_t w) { return (w >> 24) & 0xF; }
-__host__ __device__ constexpr uint32_t romw_cycles(uint32_t w) { return (w >> 28) & 7; }
 
-// ---------------------------------------------------------------- cold paths
-// Collision bits among live objects over visible columns [lo, hi) of one line.
-__device__ __noinline__ uint32_t fc_collide_cols(const uint8_t *tia, uint32_t E, uint32_t live, uint32_t lo,
-                                                 uint32_t hi) {
-  auto R = [&](uint32_t s) { return (uint32_t)tia[s * E]; };
+// Shared-memory views of one env's TIA file and I/O state.
+struct IoCtx {
+  uint8_t *tia;
+  uint32_t *io;
+  uint32_t E;
+  __device__ __forceinline__ uint32_t T(uint32_t s) const { return tia[s * E]; }
+  __device__ __forceinline__ void Tset(uint32_t s, uint32_t v) const { tia[s * E] = (uint8_t)v; }
+  __device__ __forceinline__ uint32_t G(uint32_t w) const { return io[w * E]; }
+  __device__ __forceinline__ void Sset(uint32_t w, uint32_t v) const { io[w * E] = v; }
+  __device__ __forceinline__ uint64_t G64(uint32_t w) const {
+    return (uint64_t)io[w * E] | (uint64_t)io[(w + 1) * E] << 32;
+  }
+  __device__ __forceinline__ void S64(uint32_t w, uint64_t v) const {
+    io[w * E] = (uint32_t)v;
+    io[(w + 1) * E] = (uint32_t)(v >> 32);
+  }
+};
+
+// ---------------------------------------------------------------- collisions (cold)
+__device__ __noinline__ uint32_t fc_collide_cols(IoCtx c, uint32_t live, uint32_t lo, uint32_t hi) {
   M160 r{range_word(0, lo, hi), range_word(1, lo, hi), range_word(2, lo, hi), range_word(3, lo, hi),
          range_word(4, lo, hi)};
   M160 z{0, 0, 0, 0, 0};
-  const uint32_t nus0 = R(T_NUSIZ0), nus1 = R(T_NUSIZ1), ctrl = R(T_CTRLPF);
-  M160 p0 = (live & 1) ? player_mask((R(T_VDELP0) & 1) ? R(T_GRP0_O) : R(T_GRP0_N), R(T_REFP0), nus0, R(T_P0)) : z;
-  M160 p1 = (live & 2) ? player_mask((R(T_VDELP1) & 1) ? R(T_GRP1_O) : R(T_GRP1_N), R(T_REFP1), nus1, R(T_P1)) : z;
-  M160 m0 = (live & 4) ? missile_mask(nus0, R(T_M0)) : z;
-  M160 m1 = (live & 8) ? missile_mask(nus1, R(T_M1)) : z;
-  M160 b = (live & 16) ? ball_mask(ctrl, R(T_BL)) : z;
-  M160 f = (live & 32) ? pf_mask(R(T_PF0), R(T_PF1), R(T_PF2), ctrl) : z;
-  uint32_t c = 0;
-  c |= (uint32_t)meet(m0, p1, r) << 1 | (uint32_t)meet(m0, p0, r) << 0;
-  c |= (uint32_t)meet(m1, p0, r) << 3 | (uint32_t)meet(m1, p1, r) << 2;
-  c |= (uint32_t)meet(p0, f, r) << 5 | (uint32_t)meet(p0, b, r) << 4;
-  c |= (uint32_t)meet(p1, f, r) << 7 | (uint32_t)meet(p1, b, r) << 6;
-  c |= (uint32_t)meet(m0, f, r) << 9 | (uint32_t)meet(m0, b, r) << 8;
-  c |= (uint32_t)meet(m1, f, r) << 11 | (uint32_t)meet(m1, b, r) << 10;
-  c |= (uint32_t)meet(b, f, r) << 13;
-  c |= (uint32_t)meet(p0, p1, r) << 15 | (uint32_t)meet(m0, m1, r) << 14;
-  return c;
+  const uint32_t nus0 = c.T(T_NUSIZ0), nus1 = c.T(T_NUSIZ1), ctrl = c.T(T_CTRLPF);
+  M160 p0 = (live & 1) ? player_mask((c.T(T_VDELP0) & 1) ? c.T(T_GRP0_O) : c.T(T_GRP0_N), c.T(T_REFP0), nus0,
+                                     c.T(T_P0))
+                       : z;
+  M160 p1 = (live & 2) ? player_mask((c.T(T_VDELP1) & 1) ? c.T(T_GRP1_O) : c.T(T_GRP1_N), c.T(T_REFP1), nus1,
+                                     c.T(T_P1))
+                       : z;
+  M160 m0 = (live & 4) ? missile_mask(nus0, c.T(T_M0)) : z;
+  M160 m1 = (live & 8) ? missile_mask(nus1, c.T(T_M1)) : z;
+  M160 b = (live & 16) ? ball_mask(ctrl, c.T(T_BL)) : z;
+  M160 f = (live & 32) ? pf_mask(c.T(T_PF0), c.T(T_PF1), c.T(T_PF2), ctrl) : z;
+  uint32_t x = 0;
+  x |= (uint32_t)meet(m0, p1, r) << 1 | (uint32_t)meet(m0, p0, r) << 0;
+  x |= (uint32_t)meet(m1, p0, r) << 3 | (uint32_t)meet(m1, p1, r) << 2;
+  x |= (uint32_t)meet(p0, f, r) << 5 | (uint32_t)meet(p0, b, r) << 4;
+  x |= (uint32_t)meet(p1, f, r) << 7 | (uint32_t)meet(p1, b, r) << 6;
+  x |= (uint32_t)meet(m0, f, r) << 9 | (uint32_t)meet(m0, b, r) << 8;
+  x |= (uint32_t)meet(m1, f, r) << 11 | (uint32_t)meet(m1, b, r) << 10;
+  x |= (uint32_t)meet(b, f, r) << 13;
+  x |= (uint32_t)meet(p0, p1, r) << 15 | (uint32_t)meet(m0, m1, r) << 14;
+  return x;
 }
 
-// Collisions over the color clocks [from, upto) (frame-relative), state constant.
-__device__ __noinline__ uint32_t fc_collide_span(const uint8_t *tia, uint32_t E, uint32_t live, uint32_t from,
-                                                 uint32_t upto, uint64_t L0, uint64_t bar) {
-  uint32_t la = from / 228u, xa = from - la * 228u;
-  uint32_t lb = upto / 228u, xb = upto - lb * 228u;
-  uint32_t c = 0;
+__device__ __forceinline__ uint32_t fc_live(IoCtx c) {
+  const uint32_t g0 = (c.T(T_VDELP0) & 1) ? c.T(T_GRP0_O) : c.T(T_GRP0_N);
+  const uint32_t g1 = (c.T(T_VDELP1) & 1) ? c.T(T_GRP1_O) : c.T(T_GRP1_N);
+  const uint32_t eb = (c.T(T_VDELBL) & 1) ? c.T(T_ENABL_O) : c.T(T_ENABL_N);
+  return (g0 ? 1u : 0u) | (g1 ? 2u : 0u) | (((c.T(T_ENAM0) & 2) && !(c.T(T_RESMP0) & 2)) ? 4u : 0u) |
+         (((c.T(T_ENAM1) & 2) && !(c.T(T_RESMP1) & 2)) ? 8u : 0u) | ((eb & 2) ? 16u : 0u) |
+         (((c.T(T_PF0) & 0xF0) | c.T(T_PF1) | c.T(T_PF2)) ? 32u : 0u);
+}
+
+// Account collisions for every color clock in [ceval, upto) (frame-relative).
+__device__ __forceinline__ void fc_cx_eval(IoCtx c, uint32_t upto) {
+  const uint32_t from = c.G(IO_CEVAL);
+  if (upto <= from) return;
+  c.Sset(IO_CEVAL, upto);
+  if (c.T(T_VBLANK) & 2) return;
+  const uint32_t live = fc_live(c);
+  if (__popc(live) < 2) return;
+  const uint64_t L0 = c.G64(IO_L0LO), bar = c.G64(IO_BARLO);
+  const uint32_t la = from / 228u, xa = from - la * 228u;
+  const uint32_t lb = upto / 228u, xb = upto - lb * 228u;
+  uint32_t x = 0;
   auto seg = [&](uint32_t line, uint32_t x0, uint32_t x1) {
     if (x1 <= 68) return;
     uint32_t lo = x0 > 68 ? x0 - 68 : 0, hi = x1 - 68;
     if (L0 + line == bar && lo < 8) lo = 8;
-    if (lo < hi) c |= fc_collide_cols(tia, E, live, lo, hi);
+    if (lo < hi) x |= fc_collide_cols(c, live, lo, hi);
   };
   if (la == lb) {
     seg(la, xa, xb);
@@ -78,26 +120,143 @@ __device__ __noinline__ uint32_t fc_collide_span(const uint8_t *tia, uint32_t E,
     if (lb > la + 1) seg(la + 1, 0, 228);
     if (xb) seg(lb, 0, xb);
   }
-  return c;
+  c.Sset(IO_CX, c.G(IO_CX) | x);
 }
 
-__device__ __noinline__ uint32_t fc_riot_read(uint32_t addr, uint64_t now, uint32_t ports, uint32_t joy,
-                                              uint64_t tim_cw, uint32_t tim_v, uint32_t tim_shift) {
-  const uint32_t swcha_out = ports & 0xFF, swacnt = (ports >> 8) & 0xFF, swchb_out = (ports >> 16) & 0xFF,
-                 swbcnt = ports >> 24;
-  if (!(addr & 4)) {
-    switch (addr & 3) {
-      case 0: return ((swcha_out & swacnt) | (joy & ~swacnt)) & 0xFF;
-      case 1: return swacnt;
-      case 2: return ((swchb_out & swbcnt) | (0x0Bu & ~swbcnt)) & 0xFF;
-      default: return swbcnt;
+// ---------------------------------------------------------------- I/O (cold)
+__device__ __forceinline__ uint32_t fc_res_pos(uint32_t eff, uint32_t add, uint32_t hb) {
+  const uint32_t x = eff % 228u;
+  if (x < 68) return hb;
+  const uint32_t p = x - 68 + add;
+  return p >= 160 ? p - 160 : p;
+}
+__device__ __forceinline__ uint32_t fc_hm_move(uint32_t pos, uint32_t hm) {
+  int s = (int)((hm >> 4) & 0xF);
+  if (s >= 8) s -= 16;
+  int p = (int)pos - s;
+  p += p < 0 ? 160 : 0;
+  p -= p >= 160 ? 160 : 0;
+  return (uint32_t)p;
+}
+
+// Read a TIA or RIOT address (13-bit, neither RAM nor cartridge) at cycle t.
+__device__ __noinline__ uint32_t fc_io_read(IoCtx c, uint32_t a, uint32_t t) {
+  if (!(a & 0x80)) {
+    const uint32_t reg = a & 0x0F;
+    if (reg < 8) {
+      fc_cx_eval(c, 3u * t);
+      const uint32_t cx = c.G(IO_CX);
+      return (((cx >> (2 * reg + 1)) & 1u) << 7) | (((cx >> (2 * reg)) & 1u) << 6);
+    }
+    if (reg == 0x0C) return (c.G(IO_FIRE) || c.G(IO_LATCH)) ? 0x00u : 0x80u;
+    if (reg == 0x0D) return 0x80u;
+    return 0;
+  }
+  const uint32_t ports = c.G(IO_PORTS);
+  if (!(a & 4)) {
+    const uint32_t sh = 8 * (a & 2);             // SWCHA/SWACNT in bytes 0/1, SWCHB/SWBCNT in 2/3
+    const uint32_t out = (ports >> sh) & 0xFF, ddr = (ports >> (sh + 8)) & 0xFF;
+    if (a & 1) return ddr;
+    const uint32_t pins = (a & 2) ? 0x0Bu : c.G(IO_JOY);
+    return ((out & ddr) | (pins & ~ddr)) & 0xFF;
+  }
+  const uint64_t now = 76ull * c.G64(IO_L0LO) + t;
+  const uint64_t n = now - (c.G64(IO_TCWLO) + 1);
+  const uint32_t tv = c.G(IO_TV), sh = c.G(IO_TSH);
+  const uint64_t span = (uint64_t)(tv + 1) << sh;
+  if (a & 1) return n >= span ? 0x80u : 0u;
+  if (n < span) return tv - (uint32_t)(n >> sh);
+  return (uint32_t)(0xFFull - (n - span)) & 0xFF;
+}
+
+// Write a TIA or RIOT address at cycle t; returns IO_WSYNC / IO_VSYNC_RISE.
+__device__ __noinline__ uint32_t fc_io_write(IoCtx c, uint32_t a, uint32_t v, uint32_t t) {
+  if (a & 0x80) {  // RIOT
+    if (!(a & 4)) {
+      const uint32_t sh = 8 * (a & 3);
+      c.Sset(IO_PORTS, (c.G(IO_PORTS) & ~(0xFFu << sh)) | (v & 0xFF) << sh);
+    } else if (a & 0x10) {
+      const uint32_t sel = a & 3;
+      c.Sset(IO_TV, v & 0xFF);
+      c.Sset(IO_TSH, sel == 0 ? 0 : sel == 1 ? 3 : sel == 2 ? 6 : 10);
+      c.S64(IO_TCWLO, 76ull * c.G64(IO_L0LO) + t);
+    }
+    return 0;
+  }
+  const uint32_t reg = a & 0x3F;
+  const uint32_t eff = 3u * (t + 1u);
+  if ((COLL_REGS >> reg) & 1ull) fc_cx_eval(c, eff);
+  if ((LOG_REGS >> reg) & 1ull) {
+    const uint32_t lo = c.G(IO_LOGLO), hi = c.G(IO_LOGHI);
+    if (lo | hi) {
+      uint32_t *lp = reinterpret_cast<uint32_t *>((uint64_t)lo | (uint64_t)hi << 32);
+      const uint32_t nrec = c.G(IO_LOGN);
+      if (nrec < c.G(IO_LOGCAP)) lp[nrec] = eff << 14 | reg << 8 | v;
+      else c.Sset(IO_STATUS, c.G(IO_STATUS) | ST_LOG_OVERFLOW);
+      c.Sset(IO_LOGN, nrec + 1);
     }
   }
-  uint64_t n = now - (tim_cw + 1);
-  uint64_t span = (uint64_t)(tim_v + 1) << tim_shift;
-  if (addr & 1) return n >= span ? 0x80u : 0u;
-  if (n < span) return tim_v - (uint32_t)(n >> tim_shift);
-  return (uint32_t)(0xFFull - (n - span)) & 0xFF;
+  uint32_t flags = 0;
+  switch (reg) {
+    case 0x00:
+      if (!(c.T(T_VSYNC) & 2) && (v & 2)) flags |= IO_VSYNC_RISE;
+      c.Tset(T_VSYNC, v);
+      break;
+    case 0x01:
+      c.Tset(T_VBLANK, v);
+      if (!(v & 0x40)) c.Sset(IO_LATCH, 0);
+      else if (c.G(IO_FIRE)) c.Sset(IO_LATCH, 1);
+      break;
+    case 0x02: flags |= IO_WSYNC; break;
+    case 0x04: case 0x05: case 0x06: case 0x07: case 0x08: case 0x09: case 0x0A: case 0x0B: case 0x0C:
+    case 0x0D: case 0x0E: case 0x0F:
+      c.Tset(reg - 2, v); break;                 // NUSIZ0 .. PF2 are slots 2 .. 13
+    case 0x10: c.Tset(T_P0, fc_res_pos(eff, 5, 3)); break;
+    case 0x11: c.Tset(T_P1, fc_res_pos(eff, 5, 3)); break;
+    case 0x12: c.Tset(T_M0, fc_res_pos(eff, 4, 2)); break;
+    case 0x13: c.Tset(T_M1, fc_res_pos(eff, 4, 2)); break;
+    case 0x14: c.Tset(T_BL, fc_res_pos(eff, 4, 2)); break;
+    case 0x1B: c.Tset(T_GRP1_O, c.T(T_GRP1_N)); c.Tset(T_GRP0_N, v); break;
+    case 0x1C:
+      c.Tset(T_GRP0_O, c.T(T_GRP0_N)); c.Tset(T_ENABL_O, c.T(T_ENABL_N)); c.Tset(T_GRP1_N, v); break;
+    case 0x1D: c.Tset(T_ENAM0, v); break;
+    case 0x1E: c.Tset(T_ENAM1, v); break;
+    case 0x1F: c.Tset(T_ENABL_N, v); break;
+    case 0x20: case 0x21: case 0x22: case 0x23: case 0x24: c.Tset(T_HMP0 + (reg - 0x20), v); break;
+    case 0x25: c.Tset(T_VDELP0, v); break;
+    case 0x26: c.Tset(T_VDELP1, v); break;
+    case 0x27: c.Tset(T_VDELBL, v); break;
+    case 0x28: case 0x29: {
+      const uint32_t i = reg - 0x28;
+      if ((c.T(T_RESMP0 + i) & 2) && !(v & 2)) {
+        const uint32_t nus = c.T(T_NUSIZ0 + i);
+        const uint32_t sc = (nus & 7) == 5 ? 8u : (nus & 7) == 7 ? 16u : 4u;
+        c.Tset(T_M0 + i, (c.T(T_P0 + i) + sc) % 160u);
+      }
+      c.Tset(T_RESMP0 + i, v);
+      break;
+    }
+    case 0x2A:
+      for (uint32_t o = 0; o < 5; ++o) c.Tset(T_P0 + o, fc_hm_move(c.T(T_P0 + o), c.T(T_HMP0 + o)));
+      if (eff % 228u < 68u) c.S64(IO_BARLO, c.G64(IO_L0LO) + eff / 228u);
+      break;
+    case 0x2B:
+      for (uint32_t o = 0; o < 5; ++o) c.Tset(T_HMP0 + o, 0);
+      break;
+    case 0x2C:
+      if (eff > c.G(IO_CEVAL)) c.Sset(IO_CEVAL, eff);
+      c.Sset(IO_CX, 0);
+      break;
+    default: break;  // RSYNC, audio, unused addresses
+  }
+  return flags;
+}
+
+// End of a frame: collisions up to the current cycle, then rebase to the next frame.
+__device__ __noinline__ void fc_frame_end(IoCtx c, uint32_t kf, uint32_t next_rel) {
+  fc_cx_eval(c, 3u * kf);
+  c.S64(IO_L0LO, c.G64(IO_L0LO) + next_rel);
+  c.Sset(IO_CEVAL, c.G(IO_CEVAL) - 228u * next_rel);
 }
 
 // ---------------------------------------------------------------- the console
@@ -105,31 +264,19 @@ struct FastConsole;
 __device__ __forceinline__ void fc_exec_general(FastConsole *self);
 
 struct FastConsole {
-  // shared-memory views
   const uint32_t *romw;    // staged cartridge words (banks of 4096)
-  const uint8_t *dec_op;   // opcode -> operation
+  const uint8_t *dec_op;   // general decoder: opcode -> operation, then mode/cycles/penalty
   uint32_t *ram;           // &ram_block[env], stride E words
-  uint8_t *tia;            // &tia_block[env], stride E bytes
+  IoCtx io;
   uint32_t E;
-  // CPU
   uint32_t A, X, Y, SP, PC, fc, fv, fn, fz, fdi;  // fdi holds the D (0x08) and I (0x04) bits
   uint32_t bank, jam, scheme;
   uint32_t kf;             // CPU cycles since the first line of the frame
-  uint64_t L0;             // first line of the frame
-  // RIOT
-  uint64_t tim_cw;
-  uint32_t tim_v, tim_shift, ports, joy, fire, latch;
-  // TIA shadows used by the collision-liveness test
-  uint32_t vsync, vblank, g0n, g0o, g1n, g1o, ebn, ebo, vd, en, rm, pf0, pf1, pf2;
-  uint32_t cx, ceval;
-  uint64_t bar;
-  uint32_t frame_no, status, instret;
-  uint32_t wsync, vs_rise, vs_kf;
-  uint32_t *logp;
-  uint32_t logn, logcap;
+  uint32_t pend;           // I/O flags of the current instruction
+  uint32_t vs_kf;          // cycle of a VSYNC rise in this frame, ~0 if none
+  uint32_t status, instret, frame_no;
+  uint32_t wmask;          // lanes of this warp running envs (cycle-synchronised issue)
 
-  __device__ __forceinline__ uint32_t T(uint32_t s) const { return tia[s * E]; }
-  __device__ __forceinline__ void Tset(uint32_t s, uint32_t v) { tia[s * E] = (uint8_t)v; }
   __device__ __forceinline__ uint32_t P() const {
     return (fn & 0x80) | fv | 0x20 | fdi | ((fz & 0xFF) ? 0u : 2u) | fc;
   }
@@ -140,68 +287,64 @@ struct FastConsole {
   // ---- canonical state I/O ----
   __device__ void load(const uint8_t *s) {
     const uint32_t *w = reinterpret_cast<const uint32_t *>(s);
-    uint32_t w0 = w[0], w1 = w[1];
+    const uint32_t w0 = w[0], w1 = w[1];
     A = w0 & 0xFF; X = (w0 >> 8) & 0xFF; Y = (w0 >> 16) & 0xFF; SP = w0 >> 24;
     setP(w1 & 0xFF); bank = (w1 >> 8) & 0xFF; PC = w1 >> 16;
-    uint64_t k = (uint64_t)w[2] | (uint64_t)w[3] << 32;
-    tim_cw = (uint64_t)w[4] | (uint64_t)w[5] << 32;
-    uint32_t w6 = w[6], w7 = w[7];
-    tim_v = w6 & 0xFF; tim_shift = (w6 >> 8) & 0xFF;
-    ports = (w6 >> 16) | ((w7 & 0xFFFF) << 16);     // SWCHA out, SWACNT, SWCHB out, SWBCNT
-    jam = (w7 >> 16) & 0xFF; latch = w7 >> 24;
+    const uint64_t k = (uint64_t)w[2] | (uint64_t)w[3] << 32;
+    io.Sset(IO_TCWLO, w[4]); io.Sset(IO_TCWHI, w[5]);
+    const uint32_t w6 = w[6], w7 = w[7];
+    io.Sset(IO_TV, w6 & 0xFF); io.Sset(IO_TSH, (w6 >> 8) & 0xFF);
+    io.Sset(IO_PORTS, (w6 >> 16) | ((w7 & 0xFFFF) << 16));
+    jam = (w7 >> 16) & 0xFF;
+    io.Sset(IO_LATCH, w7 >> 24);
 #pragma unroll
-    for (int q = 0; q < 10; ++q) {                 // bytes 0x20..0x47 -> TIA file (37 bytes used)
-      uint32_t v = w[8 + q];
+    for (int q = 0; q < 10; ++q) {
+      const uint32_t v = w[8 + q];
 #pragma unroll
       for (int b = 0; b < 4; ++b)
-        if (q * 4 + b < 37) tia[(q * 4 + b) * E] = (uint8_t)(v >> (8 * b));
+        if (q * 4 + b < 37) io.Tset(q * 4 + b, v >> (8 * b));
     }
-    cx = w[17] >> 16;
-    bar = (uint64_t)w[18] | (uint64_t)w[19] << 32;
-    L0 = (uint64_t)w[20] | (uint64_t)w[21] << 32;
+    io.Sset(IO_CX, w[17] >> 16);
+    io.Sset(IO_BARLO, w[18]); io.Sset(IO_BARHI, w[19]);
+    io.Sset(IO_L0LO, w[20]); io.Sset(IO_L0HI, w[21]);
     frame_no = w[22];
+    const uint64_t L0 = (uint64_t)w[20] | (uint64_t)w[21] << 32;
     kf = (uint32_t)(k - 76ull * L0);
-    ceval = 3u * kf;
-    vsync = T(T_VSYNC); vblank = T(T_VBLANK);
-    g0n = T(T_GRP0_N); g0o = T(T_GRP0_O); g1n = T(T_GRP1_N); g1o = T(T_GRP1_O);
-    ebn = T(T_ENABL_N); ebo = T(T_ENABL_O);
-    vd = (T(T_VDELP0) & 1) | (T(T_VDELP1) & 1) << 1 | (T(T_VDELBL) & 1) << 2;
-    en = (T(T_ENAM0) >> 1 & 1) | (T(T_ENAM1) & 2);
-    rm = (T(T_RESMP0) >> 1 & 1) | (T(T_RESMP1) & 2);
-    pf0 = T(T_PF0); pf1 = T(T_PF1); pf2 = T(T_PF2);
+    io.Sset(IO_CEVAL, 3u * kf);
+    io.Sset(IO_JOY, 0xFF); io.Sset(IO_FIRE, 0);
+    io.Sset(IO_LOGLO, 0); io.Sset(IO_LOGHI, 0); io.Sset(IO_LOGN, 0); io.Sset(IO_LOGCAP, 0);
+    io.Sset(IO_STATUS, 0);
     const uint4 *r4 = reinterpret_cast<const uint4 *>(s + S::RAM);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      uint4 v = r4[q];
-      uint32_t ws[4] = {v.x, v.y, v.z, v.w};
+      const uint4 v = r4[q];
+      const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
       for (int b = 0; b < 16; ++b) ram[(q * 16 + b) * E] = (ws[b >> 2] >> (8 * (b & 3))) & 0xFF;
     }
-    status = 0;
-    instret = 0;
-    joy = 0xFF;
-    fire = 0;
-    logp = nullptr;
+    status = 0; instret = 0; pend = 0; vs_kf = ~0u;
   }
   __device__ void store(uint8_t *s) const {
     uint32_t *w = reinterpret_cast<uint32_t *>(s);
+    const uint64_t L0 = io.G64(IO_L0LO);
     w[0] = A | X << 8 | Y << 16 | SP << 24;
     w[1] = P() | bank << 8 | PC << 16;
-    uint64_t k = 76ull * L0 + kf;
+    const uint64_t k = 76ull * L0 + kf;
     w[2] = (uint32_t)k; w[3] = (uint32_t)(k >> 32);
-    w[4] = (uint32_t)tim_cw; w[5] = (uint32_t)(tim_cw >> 32);
-    w[6] = tim_v | tim_shift << 8 | (ports & 0xFFFF) << 16;
-    w[7] = (ports >> 16) | jam << 16 | latch << 24;
+    w[4] = io.G(IO_TCWLO); w[5] = io.G(IO_TCWHI);
+    const uint32_t ports = io.G(IO_PORTS);
+    w[6] = io.G(IO_TV) | io.G(IO_TSH) << 8 | (ports & 0xFFFF) << 16;
+    w[7] = (ports >> 16) | jam << 16 | io.G(IO_LATCH) << 24;
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
       uint32_t v = 0;
 #pragma unroll
       for (int b = 0; b < 4; ++b)
-        if (q * 4 + b < 37) v |= (uint32_t)tia[(q * 4 + b) * E] << (8 * b);
-      if (q == 9) v = (v & 0xFFFFu) | cx << 16;   // 0x46: collision latches (0x45 is zero)
+        if (q * 4 + b < 37) v |= io.T(q * 4 + b) << (8 * b);
+      if (q == 9) v = (v & 0xFFFFu) | io.G(IO_CX) << 16;
       w[8 + q] = v;
     }
-    w[18] = (uint32_t)bar; w[19] = (uint32_t)(bar >> 32);
+    w[18] = io.G(IO_BARLO); w[19] = io.G(IO_BARHI);
     w[20] = (uint32_t)L0; w[21] = (uint32_t)(L0 >> 32);
     w[22] = frame_no; w[23] = 0;
     uint4 *r4 = reinterpret_cast<uint4 *>(s + S::RAM);
@@ -218,7 +361,6 @@ struct FastConsole {
       r4[q] = make_uint4(ws[0], ws[1], ws[2], ws[3]);
     }
   }
-  // Render-state snapshot (canonical bytes 0x20..0x5F) for the replay.
   __device__ void snapshot(uint8_t *o) const {
     uint32_t v[16];
 #pragma unroll
@@ -226,19 +368,27 @@ struct FastConsole {
       uint32_t x = 0;
 #pragma unroll
       for (int b = 0; b < 4; ++b)
-        if (q * 4 + b < 37) x |= (uint32_t)tia[(q * 4 + b) * E] << (8 * b);
+        if (q * 4 + b < 37) x |= io.T(q * 4 + b) << (8 * b);
       v[q] = x;
     }
     v[9] &= 0xFFu;
-    v[10] = (uint32_t)bar; v[11] = (uint32_t)(bar >> 32);
-    v[12] = (uint32_t)L0; v[13] = (uint32_t)(L0 >> 32);
+    v[10] = io.G(IO_BARLO); v[11] = io.G(IO_BARHI);
+    v[12] = io.G(IO_L0LO); v[13] = io.G(IO_L0HI);
     v[14] = 0; v[15] = 0;
     uint4 *d = reinterpret_cast<uint4 *>(o);
 #pragma unroll
     for (int q = 0; q < 4; ++q) d[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   }
+  __device__ void set_log(uint32_t *p, uint32_t cap) {
+    io.Sset(IO_LOGLO, (uint32_t)(uint64_t)p);
+    io.Sset(IO_LOGHI, (uint32_t)((uint64_t)p >> 32));
+    io.Sset(IO_LOGN, 0);
+    io.Sset(IO_LOGCAP, cap);
+  }
+  __device__ uint32_t log_count() const { return io.G(IO_LOGN); }
+  __device__ uint32_t all_status() const { return status | io.G(IO_STATUS); }
 
-  __device__ __forceinline__ void apply_action(uint32_t a) {
+  __device__ void apply_action(uint32_t a) {
     uint32_t d;
     switch (a) {
       case 2: case 10: d = 1; break;
@@ -251,128 +401,11 @@ struct FastConsole {
       case 9: case 17: d = 12; break;
       default: d = 0; break;
     }
-    joy = 0xFFu & ~(((d & 2) ? 0x80u : 0u) | ((d & 4) ? 0x40u : 0u) | ((d & 8) ? 0x20u : 0u) | ((d & 1) ? 0x10u : 0u));
-    fire = (a == 1 || a >= 10) ? 1u : 0u;
-    if (fire && (vblank & 0x40)) latch = 1;
-  }
-
-  // ---- collisions ----
-  __device__ __forceinline__ uint32_t live() const {
-    uint32_t g0 = (vd & 1) ? g0o : g0n, g1 = (vd & 2) ? g1o : g1n, eb = (vd & 4) ? ebo : ebn;
-    return (g0 ? 1u : 0u) | (g1 ? 2u : 0u) | ((en & ~rm) & 3u) << 2 | (eb & 2u) << 3 |
-           (((pf0 & 0xF0) | pf1 | pf2) ? 32u : 0u);
-  }
-  __device__ __forceinline__ void cx_eval(uint32_t upto) {
-    uint32_t from = ceval;
-    if (upto <= from) return;
-    ceval = upto;
-    if (vblank & 2) return;
-    uint32_t l = live();
-    if (__popc(l) < 2) return;
-    cx |= fc_collide_span(tia, E, l, from, upto, L0, bar);
-  }
-
-  // ---- TIA ----
-  __device__ __forceinline__ static uint32_t res_pos(uint32_t eff, uint32_t add, uint32_t hb) {
-    uint32_t x = eff % 228u;
-    if (x < 68) return hb;
-    uint32_t p = x - 68 + add;
-    return p >= 160 ? p - 160 : p;
-  }
-  __device__ __forceinline__ static uint32_t hm_move(uint32_t pos, uint32_t hm) {
-    int s = (int)((hm >> 4) & 0xF);
-    if (s >= 8) s -= 16;
-    int p = (int)pos - s;
-    p += p < 0 ? 160 : 0;
-    p -= p >= 160 ? 160 : 0;
-    return (uint32_t)p;
-  }
-  __device__ void tia_write(uint32_t reg, uint32_t v, uint32_t t) {
-    const uint32_t eff = 3u * (t + 1u);
-    if ((COLL_REGS >> reg) & 1ull) cx_eval(eff);
-    if (logp && ((LOG_REGS >> reg) & 1ull)) {
-      if (logn < logcap) logp[logn] = eff << 14 | reg << 8 | v;
-      else status |= ST_LOG_OVERFLOW;
-      logn++;
-    }
-    switch (reg) {
-      case 0x00:
-        if (!(vsync & 2) && (v & 2)) { vs_rise = 1; vs_kf = t; }
-        vsync = v; Tset(T_VSYNC, v); break;
-      case 0x01:
-        vblank = v; Tset(T_VBLANK, v);
-        if (!(v & 0x40)) latch = 0;
-        else if (fire) latch = 1;
-        break;
-      case 0x02: wsync = 1; break;
-      case 0x04: case 0x05: case 0x06: case 0x07: case 0x08: case 0x09: case 0x0A: case 0x0B: case 0x0C:
-        Tset(reg - 2, v); break;                    // NUSIZ0 .. REFP1 are slots 2 .. 10
-      case 0x0D: pf0 = v; Tset(T_PF0, v); break;
-      case 0x0E: pf1 = v; Tset(T_PF1, v); break;
-      case 0x0F: pf2 = v; Tset(T_PF2, v); break;
-      case 0x10: Tset(T_P0, res_pos(eff, 5, 3)); break;
-      case 0x11: Tset(T_P1, res_pos(eff, 5, 3)); break;
-      case 0x12: Tset(T_M0, res_pos(eff, 4, 2)); break;
-      case 0x13: Tset(T_M1, res_pos(eff, 4, 2)); break;
-      case 0x14: Tset(T_BL, res_pos(eff, 4, 2)); break;
-      case 0x1B: g0n = v; g1o = g1n; Tset(T_GRP0_N, v); Tset(T_GRP1_O, g1o); break;
-      case 0x1C: g1n = v; g0o = g0n; ebo = ebn; Tset(T_GRP1_N, v); Tset(T_GRP0_O, g0o); Tset(T_ENABL_O, ebo); break;
-      case 0x1D: en = (en & ~1u) | (v >> 1 & 1); Tset(T_ENAM0, v); break;
-      case 0x1E: en = (en & ~2u) | (v & 2); Tset(T_ENAM1, v); break;
-      case 0x1F: ebn = v; Tset(T_ENABL_N, v); break;
-      case 0x20: case 0x21: case 0x22: case 0x23: case 0x24: Tset(T_HMP0 + (reg - 0x20), v); break;
-      case 0x25: vd = (vd & ~1u) | (v & 1); Tset(T_VDELP0, v); break;
-      case 0x26: vd = (vd & ~2u) | (v & 1) << 1; Tset(T_VDELP1, v); break;
-      case 0x27: vd = (vd & ~4u) | (v & 1) << 2; Tset(T_VDELBL, v); break;
-      case 0x28: case 0x29: {
-        const uint32_t i = reg - 0x28;
-        const uint32_t old = T(T_RESMP0 + i);
-        if ((old & 2) && !(v & 2)) {
-          uint32_t nus = T(T_NUSIZ0 + i);
-          uint32_t sc = (nus & 7) == 5 ? 8u : (nus & 7) == 7 ? 16u : 4u;
-          Tset(T_M0 + i, (T(T_P0 + i) + sc) % 160u);
-        }
-        Tset(T_RESMP0 + i, v);
-        rm = (rm & ~(1u << i)) | ((v >> 1) & 1) << i;
-        break;
-      }
-      case 0x2A:
-#pragma unroll
-        for (uint32_t o = 0; o < 5; ++o) Tset(T_P0 + o, hm_move(T(T_P0 + o), T(T_HMP0 + o)));
-        if (eff % 228u < 68u) bar = L0 + eff / 228u;
-        break;
-      case 0x2B:
-#pragma unroll
-        for (uint32_t o = 0; o < 5; ++o) Tset(T_HMP0 + o, 0);
-        break;
-      case 0x2C:
-        if (eff > ceval) ceval = eff;
-        cx = 0;
-        break;
-      default: break;
-    }
-  }
-  __device__ __forceinline__ uint32_t tia_read(uint32_t reg, uint32_t t) {
-    if (reg < 8) {
-      cx_eval(3u * t);
-      return (((cx >> (2 * reg + 1)) & 1u) << 7) | (((cx >> (2 * reg)) & 1u) << 6);
-    }
-    if (reg == 0x0C) return (fire || latch) ? 0x00u : 0x80u;
-    if (reg == 0x0D) return 0x80u;
-    return 0;
-  }
-  __device__ __forceinline__ void riot_write(uint32_t addr, uint32_t v, uint32_t t) {
-    if (!(addr & 4)) {
-      const uint32_t sh = 8 * (addr & 3);
-      ports = (ports & ~(0xFFu << sh)) | (v & 0xFF) << sh;
-      return;
-    }
-    if (addr & 0x10) {
-      tim_v = v;
-      const uint32_t sel = addr & 3;
-      tim_shift = sel == 0 ? 0 : sel == 1 ? 3 : sel == 2 ? 6 : 10;
-      tim_cw = 76ull * L0 + t;
-    }
+    io.Sset(IO_JOY, 0xFFu & ~(((d & 2) ? 0x80u : 0u) | ((d & 4) ? 0x40u : 0u) | ((d & 8) ? 0x20u : 0u) |
+                              ((d & 1) ? 0x10u : 0u)));
+    const uint32_t fire = (a == 1 || a >= 10) ? 1u : 0u;
+    io.Sset(IO_FIRE, fire);
+    if (fire && (io.T(T_VBLANK) & 0x40)) io.Sset(IO_LATCH, 1);
   }
 
   // ---- bus ----
@@ -380,47 +413,57 @@ struct FastConsole {
     if (scheme == 1) { if (off == 0xFF8 || off == 0xFF9) bank = off - 0xFF8; }
     else if (scheme == 2) { if (off >= 0xFF6 && off <= 0xFF9) bank = off - 0xFF6; }
   }
-  __device__ uint32_t rd_slow(uint32_t addr, uint32_t t) {
-    if (addr & 0x1000) {
-      const uint32_t off = addr & 0xFFF;
+  __device__ __forceinline__ void note_vsync(uint32_t t) {
+    if (vs_kf == ~0u) vs_kf = t;
+  }
+  // zero-page access: RAM for $80-$FF, TIA below
+  __device__ __forceinline__ uint32_t rdz(uint32_t z, uint32_t t) {
+    return (z & 0x80) ? ram[(z & 0x7F) * E] : fc_io_read(io, z, t);
+  }
+  __device__ __forceinline__ void wrz(uint32_t z, uint32_t v, uint32_t t) {
+    if (z & 0x80) {
+      ram[(z & 0x7F) * E] = v & 0xFF;
+    } else {
+      const uint32_t f = fc_io_write(io, z, v & 0xFF, t);
+      pend |= f;
+      if (f & IO_VSYNC_RISE) note_vsync(t);
+    }
+  }
+  __device__ __forceinline__ uint32_t rd(uint32_t addr, uint32_t t) {
+    const uint32_t a = addr & 0x1FFF;
+    if ((a & 0x1280) == 0x0080) return ram[(a & 0x7F) * E];
+    if (a & 0x1000) {
+      const uint32_t off = a & 0xFFF;
       if (scheme) hotspot(off);
       return romw[bank * 4096u + off] & 0xFF;
     }
-    if (!(addr & 0x80)) return tia_read(addr & 0x0F, t);
-    if (!(addr & 0x200)) return ram[(addr & 0x7F) * E];
-    return fc_riot_read(addr, 76ull * L0 + t, ports, joy, tim_cw, tim_v, tim_shift);
-  }
-  __device__ __forceinline__ uint32_t rd(uint32_t addr, uint32_t t) {
-    addr &= 0x1FFF;
-    if ((addr & 0x1280) == 0x0080) return ram[(addr & 0x7F) * E];
-    return rd_slow(addr, t);
+    return fc_io_read(io, a, t);
   }
   __device__ __forceinline__ void wr(uint32_t addr, uint32_t v, uint32_t t) {
-    addr &= 0x1FFF;
-    if ((addr & 0x1280) == 0x0080) { ram[(addr & 0x7F) * E] = v & 0xFF; return; }
-    if (addr & 0x1000) { if (scheme) hotspot(addr & 0xFFF); return; }
-    if (!(addr & 0x80)) { tia_write(addr & 0x3F, v & 0xFF, t); return; }
-    riot_write(addr, v, t);
+    const uint32_t a = addr & 0x1FFF;
+    if ((a & 0x1280) == 0x0080) { ram[(a & 0x7F) * E] = v & 0xFF; return; }
+    if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
+    const uint32_t f = fc_io_write(io, a, v & 0xFF, t);
+    pend |= f;
+    if (f & IO_VSYNC_RISE) note_vsync(t);
   }
-  __device__ __forceinline__ void push(uint32_t v, uint32_t t) { wr(0x100u | SP, v, t); SP = (SP - 1) & 0xFF; }
-  __device__ __forceinline__ uint32_t pull(uint32_t t) { SP = (SP + 1) & 0xFF; return rd(0x100u | SP, t); }
 
   // ---- ALU ----
   __device__ __forceinline__ void adc(uint32_t v) {
     const uint32_t c = fc;
     if (!(fdi & 0x08)) {
-      uint32_t s = A + v + c;
-      uint32_t r = s & 0xFF;
+      const uint32_t s = A + v + c;
+      const uint32_t r = s & 0xFF;
       fv = ((~(A ^ v) & (A ^ r)) & 0x80u) >> 1;
       fc = s >> 8;
       fn = fz = r;
       A = r;
       return;
     }
-    uint32_t zb = (A + v + c) & 0xFF;
+    const uint32_t zb = (A + v + c) & 0xFF;
     int lo = (int)(A & 0x0F) + (int)(v & 0x0F) + (int)c;
     if (lo > 9) lo = ((lo + 6) & 0x0F) + 0x10;
-    int hs = (int)(int8_t)(uint8_t)(A & 0xF0) + (int)(int8_t)(uint8_t)(v & 0xF0) + lo;
+    const int hs = (int)(int8_t)(uint8_t)(A & 0xF0) + (int)(int8_t)(uint8_t)(v & 0xF0) + lo;
     int hu = (int)(A & 0xF0) + (int)(v & 0xF0) + lo;
     fn = (uint32_t)hs & 0x80;
     fv = (hs > 127 || hs < -128) ? 0x40u : 0u;
@@ -450,221 +493,207 @@ struct FastConsole {
     fc = reg >= v ? 1u : 0u;
     fn = fz = (reg - v) & 0xFF;
   }
-
-
-  // ---- single bus sites of the hot path ----
-  __device__ __forceinline__ uint32_t bus_read(uint32_t ea, uint32_t t) {
-    const uint32_t a = ea & 0x1FFF;
-    if ((a & 0x1280) == 0x0080) return ram[(a & 0x7F) * E];
-    if (a & 0x1000) {
-      const uint32_t off = a & 0xFFF;
-      if (scheme) hotspot(off);
-      return romw[bank * 4096u + off] & 0xFF;
-    }
-    if (!(a & 0x80)) return tia_read(a & 0x0F, t);
-    return fc_riot_read(a, 76ull * L0 + t, ports, joy, tim_cw, tim_v, tim_shift);
-  }
-  __device__ __forceinline__ void bus_write(uint32_t ea, uint32_t v, uint32_t t) {
-    const uint32_t a = ea & 0x1FFF;
-    if ((a & 0x1280) == 0x0080) { ram[(a & 0x7F) * E] = v & 0xFF; return; }
-    if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
-    if (!(a & 0x80)) { tia_write(a & 0x3F, v & 0xFF, t); return; }
-    riot_write(a, v, t);
-  }
+  __device__ __forceinline__ uint32_t asl(uint32_t v) { fc = v >> 7; const uint32_t r = (v << 1) & 0xFF; fn = fz = r; return r; }
+  __device__ __forceinline__ uint32_t lsr(uint32_t v) { fc = v & 1; const uint32_t r = v >> 1; fn = fz = r; return r; }
+  __device__ __forceinline__ uint32_t rol(uint32_t v) { const uint32_t r = ((v << 1) | fc) & 0xFF; fc = v >> 7; fn = fz = r; return r; }
+  __device__ __forceinline__ uint32_t ror(uint32_t v) { const uint32_t r = (v >> 1) | (fc << 7); fc = v & 1; fn = fz = r; return r; }
+  __device__ __forceinline__ uint32_t inc(uint32_t v) { const uint32_t r = (v + 1) & 0xFF; fn = fz = r; return r; }
+  __device__ __forceinline__ uint32_t dec(uint32_t v) { const uint32_t r = (v - 1) & 0xFF; fn = fz = r; return r; }
 
   // ---- one instruction, hot form ----
-  // Handles every instruction whose fetch comes from the cartridge away from
-  // hotspots, except BRK, RTI, JMP (ind), stack accesses outside RAM and
-  // indirect pointers outside RAM; those run exec_general out of line on a
-  // copy of the register state.  One bus-read and one bus-write site.
+  // Returns false (with nothing changed) for the cases the general decoder
+  // takes.  Each case sets the cycle count n and the next PC; the tail
+  // applies the WSYNC stall.
   __device__ __forceinline__ bool exec() {
     const uint32_t k0 = kf;
     const uint32_t pc = PC;
     const uint32_t off = pc & 0xFFF;
-    if (!(pc & 0x1000) || off > (scheme ? 0xFF3u : 0xFFDu)) return false;
+    if (!(pc & 0x1000) || off > (scheme ? 0xFF3u : 0xFFCu)) return false;
     const uint32_t w = romw[bank * 4096u + off];
-    const uint32_t op = dec_op[w & 0xFF];
-    const uint32_t mode = romw_mode(w);
-    uint32_t n = romw_cycles(w);
-    const uint32_t b1 = (w >> 8) & 0xFF, b2 = (w >> 16) & 0xFF;
-    if (op == O_JAM || op == O_BRK || op == O_RTI || mode == IND) return false;
-    uint32_t ea = 0, cross = 0, len = 2;
-    switch (mode) {
-      case IMP: case ACC: len = 1; break;
-      case IMM: break;
-      case ZP: ea = b1; break;
-      case ZPX: ea = (b1 + X) & 0xFF; break;
-      case ZPY: ea = (b1 + Y) & 0xFF; break;
-      case ABS: ea = b1 | b2 << 8; len = 3; break;
-      case ABX: { uint32_t b = b1 | b2 << 8; ea = (b + X) & 0xFFFF; cross = (b ^ ea) >> 8; len = 3; break; }
-      case ABY: { uint32_t b = b1 | b2 << 8; ea = (b + Y) & 0xFFFF; cross = (b ^ ea) >> 8; len = 3; break; }
-      case IZX: {
-        const uint32_t z = (b1 + X) & 0xFF;
-        if (!(z & 0x80) || z == 0xFF) return false;            // pointer bytes outside RAM
-        ea = ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8;
-        break;
-      }
-      case IZY: {
-        if (!(b1 & 0x80) || b1 == 0xFF) return false;
-        const uint32_t b = ram[(b1 & 0x7F) * E] | ram[((b1 + 1) & 0x7F) * E] << 8;
-        ea = (b + Y) & 0xFFFF;
-        cross = (b ^ ea) >> 8;
-        break;
-      }
-      default: break;  // REL
+    const uint32_t b1 = (w >> 8) & 0xFF;
+    const uint32_t a16 = (w >> 8) & 0xFFFF;
+    uint32_t n;
+    pend = 0;
+#define ZPX_ ((b1 + X) & 0xFF)
+#define ZPY_ ((b1 + Y) & 0xFF)
+#define ABX_ ((a16 + X) & 0xFFFF)
+#define ABY_ ((a16 + Y) & 0xFFFF)
+#define XPG(base, ea) ((((base) ^ (ea)) >> 8) & 1u)
+#define NZ(v) (fn = fz = (v))
+// read instructions: imm, zp, zp,X, abs, abs,X, abs,Y, (zp,X), (zp),Y
+#define RD_OPS(OPI, OPZ, OPZX, OPA, OPAX, OPAY, OPIX, OPIY, BODY)                                          \
+  case OPI: { const uint32_t v = b1; BODY; n = 2; PC = pc + 2; break; }                                      \
+  case OPZ: { const uint32_t v = rdz(b1, k0 + 2); BODY; n = 3; PC = pc + 2; break; }                          \
+  case OPZX: { const uint32_t v = rdz(ZPX_, k0 + 3); BODY; n = 4; PC = pc + 2; break; }                       \
+  case OPA: { const uint32_t v = rd(a16, k0 + 3); BODY; n = 4; PC = pc + 3; break; }                          \
+  case OPAX: { const uint32_t ea = ABX_; n = 4 + XPG(a16, ea); const uint32_t v = rd(ea, k0 + n - 1); BODY;   \
+               PC = pc + 3; break; }                                                                          \
+  case OPAY: { const uint32_t ea = ABY_; n = 4 + XPG(a16, ea); const uint32_t v = rd(ea, k0 + n - 1); BODY;   \
+               PC = pc + 3; break; }                                                                          \
+  case OPIX: { const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;                          \
+               const uint32_t ea = ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8;                      \
+               const uint32_t v = rd(ea, k0 + 5); BODY; n = 6; PC = pc + 2; break; }                           \
+  case OPIY: { if (!(b1 & 0x80) || b1 == 0xFF) return false;                                                  \
+               const uint32_t base = ram[(b1 & 0x7F) * E] | ram[((b1 + 1) & 0x7F) * E] << 8;                  \
+               const uint32_t ea = (base + Y) & 0xFFFF; n = 5 + XPG(base, ea);                                \
+               const uint32_t v = rd(ea, k0 + n - 1); BODY; PC = pc + 2; break; }
+// read-modify-write: acc, zp, zp,X, abs, abs,X
+#define RMW_OPS(OPACC, OPZ, OPZX, OPA, OPAX, FN)                                                             \
+  case OPACC: { A = FN(A); n = 2; PC = pc + 1; break; }                                                       \
+  case OPZ: { const uint32_t o = rdz(b1, k0 + 2); const uint32_t r = FN(o);                                   \
+              wrz(b1, o, k0 + 3); wrz(b1, r, k0 + 4); n = 5; PC = pc + 2; break; }                            \
+  case OPZX: { const uint32_t z = ZPX_; const uint32_t o = rdz(z, k0 + 3); const uint32_t r = FN(o);          \
+               wrz(z, o, k0 + 4); wrz(z, r, k0 + 5); n = 6; PC = pc + 2; break; }                             \
+  case OPA: { const uint32_t o = rd(a16, k0 + 3); const uint32_t r = FN(o);                                   \
+              wr(a16, o, k0 + 4); wr(a16, r, k0 + 5); n = 6; PC = pc + 3; break; }                            \
+  case OPAX: { const uint32_t ea = ABX_; const uint32_t o = rd(ea, k0 + 4); const uint32_t r = FN(o);         \
+               wr(ea, o, k0 + 5); wr(ea, r, k0 + 6); n = 7; PC = pc + 3; break; }
+// memory-only read-modify-write (INC, DEC): zp, zp,X, abs, abs,X
+#define RMWM_OPS(OPZ, OPZX, OPA, OPAX, FN)                                                                   \
+  case OPZ: { const uint32_t o = rdz(b1, k0 + 2); const uint32_t r = FN(o);                                   \
+              wrz(b1, o, k0 + 3); wrz(b1, r, k0 + 4); n = 5; PC = pc + 2; break; }                            \
+  case OPZX: { const uint32_t z = ZPX_; const uint32_t o = rdz(z, k0 + 3); const uint32_t r = FN(o);          \
+               wrz(z, o, k0 + 4); wrz(z, r, k0 + 5); n = 6; PC = pc + 2; break; }                             \
+  case OPA: { const uint32_t o = rd(a16, k0 + 3); const uint32_t r = FN(o);                                   \
+              wr(a16, o, k0 + 4); wr(a16, r, k0 + 5); n = 6; PC = pc + 3; break; }                            \
+  case OPAX: { const uint32_t ea = ABX_; const uint32_t o = rd(ea, k0 + 4); const uint32_t r = FN(o);         \
+               wr(ea, o, k0 + 5); wr(ea, r, k0 + 6); n = 7; PC = pc + 3; break; }
+#define BR(OPC, COND)                                                                                          \
+  case OPC: {                                                                                                 \
+    const uint32_t nx = (pc + 2) & 0xFFFF;                                                                    \
+    n = 2; PC = nx;                                                                                           \
+    if (COND) { const uint32_t tg = (nx + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF;                   \
+                n += ((nx ^ tg) & 0xFF00) ? 2u : 1u; PC = tg; }                                               \
+    break; }
+#define IMPL(OPC, BODY) case OPC: { BODY; n = 2; PC = pc + 1; break; }
+    switch (w & 0xFF) {
+      RD_OPS(0xA9, 0xA5, 0xB5, 0xAD, 0xBD, 0xB9, 0xA1, 0xB1, { A = v; NZ(A); })            // LDA
+      RD_OPS(0x69, 0x65, 0x75, 0x6D, 0x7D, 0x79, 0x61, 0x71, { adc(v); })                  // ADC
+      RD_OPS(0xE9, 0xE5, 0xF5, 0xED, 0xFD, 0xF9, 0xE1, 0xF1, { sbc(v); })                  // SBC
+      RD_OPS(0x29, 0x25, 0x35, 0x2D, 0x3D, 0x39, 0x21, 0x31, { A &= v; NZ(A); })           // AND
+      RD_OPS(0x09, 0x05, 0x15, 0x0D, 0x1D, 0x19, 0x01, 0x11, { A |= v; NZ(A); })           // ORA
+      RD_OPS(0x49, 0x45, 0x55, 0x4D, 0x5D, 0x59, 0x41, 0x51, { A ^= v; NZ(A); })           // EOR
+      RD_OPS(0xC9, 0xC5, 0xD5, 0xCD, 0xDD, 0xD9, 0xC1, 0xD1, { cmp(A, v); })               // CMP
+      // LDX: imm, zp, zp,Y, abs, abs,Y
+      case 0xA2: X = b1; NZ(X); n = 2; PC = pc + 2; break;
+      case 0xA6: X = rdz(b1, k0 + 2); NZ(X); n = 3; PC = pc + 2; break;
+      case 0xB6: X = rdz(ZPY_, k0 + 3); NZ(X); n = 4; PC = pc + 2; break;
+      case 0xAE: X = rd(a16, k0 + 3); NZ(X); n = 4; PC = pc + 3; break;
+      case 0xBE: { const uint32_t ea = ABY_; n = 4 + XPG(a16, ea); X = rd(ea, k0 + n - 1); NZ(X); PC = pc + 3; break; }
+      // LDY: imm, zp, zp,X, abs, abs,X
+      case 0xA0: Y = b1; NZ(Y); n = 2; PC = pc + 2; break;
+      case 0xA4: Y = rdz(b1, k0 + 2); NZ(Y); n = 3; PC = pc + 2; break;
+      case 0xB4: Y = rdz(ZPX_, k0 + 3); NZ(Y); n = 4; PC = pc + 2; break;
+      case 0xAC: Y = rd(a16, k0 + 3); NZ(Y); n = 4; PC = pc + 3; break;
+      case 0xBC: { const uint32_t ea = ABX_; n = 4 + XPG(a16, ea); Y = rd(ea, k0 + n - 1); NZ(Y); PC = pc + 3; break; }
+      // CPX, CPY: imm, zp, abs
+      case 0xE0: cmp(X, b1); n = 2; PC = pc + 2; break;
+      case 0xE4: cmp(X, rdz(b1, k0 + 2)); n = 3; PC = pc + 2; break;
+      case 0xEC: cmp(X, rd(a16, k0 + 3)); n = 4; PC = pc + 3; break;
+      case 0xC0: cmp(Y, b1); n = 2; PC = pc + 2; break;
+      case 0xC4: cmp(Y, rdz(b1, k0 + 2)); n = 3; PC = pc + 2; break;
+      case 0xCC: cmp(Y, rd(a16, k0 + 3)); n = 4; PC = pc + 3; break;
+      // BIT: zp, abs
+      case 0x24: { const uint32_t v = rdz(b1, k0 + 2); fn = v; fv = v & 0x40; fz = A & v; n = 3; PC = pc + 2; break; }
+      case 0x2C: { const uint32_t v = rd(a16, k0 + 3); fn = v; fv = v & 0x40; fz = A & v; n = 4; PC = pc + 3; break; }
+      // stores
+      case 0x85: wrz(b1, A, k0 + 2); n = 3; PC = pc + 2; break;
+      case 0x95: wrz(ZPX_, A, k0 + 3); n = 4; PC = pc + 2; break;
+      case 0x8D: wr(a16, A, k0 + 3); n = 4; PC = pc + 3; break;
+      case 0x9D: wr(ABX_, A, k0 + 4); n = 5; PC = pc + 3; break;
+      case 0x99: wr(ABY_, A, k0 + 4); n = 5; PC = pc + 3; break;
+      case 0x81: { const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;
+                   wr(ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8, A, k0 + 5); n = 6; PC = pc + 2; break; }
+      case 0x91: { if (!(b1 & 0x80) || b1 == 0xFF) return false;
+                   const uint32_t base = ram[(b1 & 0x7F) * E] | ram[((b1 + 1) & 0x7F) * E] << 8;
+                   wr((base + Y) & 0xFFFF, A, k0 + 5); n = 6; PC = pc + 2; break; }
+      case 0x86: wrz(b1, X, k0 + 2); n = 3; PC = pc + 2; break;
+      case 0x96: wrz(ZPY_, X, k0 + 3); n = 4; PC = pc + 2; break;
+      case 0x8E: wr(a16, X, k0 + 3); n = 4; PC = pc + 3; break;
+      case 0x84: wrz(b1, Y, k0 + 2); n = 3; PC = pc + 2; break;
+      case 0x94: wrz(ZPX_, Y, k0 + 3); n = 4; PC = pc + 2; break;
+      case 0x8C: wr(a16, Y, k0 + 3); n = 4; PC = pc + 3; break;
+      RMW_OPS(0x0A, 0x06, 0x16, 0x0E, 0x1E, asl)
+      RMW_OPS(0x4A, 0x46, 0x56, 0x4E, 0x5E, lsr)
+      RMW_OPS(0x2A, 0x26, 0x36, 0x2E, 0x3E, rol)
+      RMW_OPS(0x6A, 0x66, 0x76, 0x6E, 0x7E, ror)
+      RMWM_OPS(0xE6, 0xF6, 0xEE, 0xFE, inc)
+      RMWM_OPS(0xC6, 0xD6, 0xCE, 0xDE, dec)
+      BR(0x10, !(fn & 0x80))
+      BR(0x30, (fn & 0x80))
+      BR(0x50, !fv)
+      BR(0x70, fv)
+      BR(0x90, !fc)
+      BR(0xB0, fc)
+      BR(0xD0, (fz & 0xFF))
+      BR(0xF0, !(fz & 0xFF))
+      IMPL(0xE8, { X = (X + 1) & 0xFF; NZ(X); })
+      IMPL(0xC8, { Y = (Y + 1) & 0xFF; NZ(Y); })
+      IMPL(0xCA, { X = (X - 1) & 0xFF; NZ(X); })
+      IMPL(0x88, { Y = (Y - 1) & 0xFF; NZ(Y); })
+      IMPL(0xAA, { X = A; NZ(X); })
+      IMPL(0xA8, { Y = A; NZ(Y); })
+      IMPL(0x8A, { A = X; NZ(A); })
+      IMPL(0x98, { A = Y; NZ(A); })
+      IMPL(0xBA, { X = SP; NZ(X); })
+      IMPL(0x9A, { SP = X; })
+      IMPL(0x18, { fc = 0; })
+      IMPL(0x38, { fc = 1; })
+      IMPL(0x58, { fdi &= ~0x04u; })
+      IMPL(0x78, { fdi |= 0x04u; })
+      IMPL(0xB8, { fv = 0; })
+      IMPL(0xD8, { fdi &= ~0x08u; })
+      IMPL(0xF8, { fdi |= 0x08u; })
+      IMPL(0xEA, {})
+      case 0x48: if (!(SP & 0x80)) return false; ram[(SP & 0x7F) * E] = A; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
+      case 0x08: if (!(SP & 0x80)) return false; ram[(SP & 0x7F) * E] = P() | 0x10u; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
+      case 0x68: { const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
+                   SP = s1; A = ram[(s1 & 0x7F) * E]; NZ(A); n = 4; PC = pc + 1; break; }
+      case 0x28: { const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
+                   SP = s1; setP(ram[(s1 & 0x7F) * E]); n = 4; PC = pc + 1; break; }
+      case 0x4C: PC = a16; n = 3; break;
+      case 0x20: { if (SP < 0x81) return false;
+                   const uint32_t ret = (pc + 2) & 0xFFFF;
+                   ram[(SP & 0x7F) * E] = ret >> 8; ram[((SP - 1) & 0x7F) * E] = ret & 0xFF;
+                   SP = (SP - 2) & 0xFF; PC = a16; n = 6; break; }
+      case 0x60: { const uint32_t s1 = (SP + 1) & 0xFF, s2 = (SP + 2) & 0xFF;
+                   if (!(s1 & 0x80) || !(s2 & 0x80)) return false;
+                   PC = ((ram[(s1 & 0x7F) * E] | ram[(s2 & 0x7F) * E] << 8) + 1) & 0xFFFF; SP = s2; n = 6; break; }
+      default: return false;  // BRK, RTI, JMP (ind), undocumented
     }
-    const uint32_t next = (pc + len) & 0xFFFF;
-    if (cross && (w >> 31)) n++;
-    if (mode == REL) {
-      uint32_t take;
-      switch (op) {
-        case O_BCC: take = fc ^ 1u; break;
-        case O_BCS: take = fc; break;
-        case O_BNE: take = (fz & 0xFF) ? 1u : 0u; break;
-        case O_BEQ: take = (fz & 0xFF) ? 0u : 1u; break;
-        case O_BVC: take = fv ? 0u : 1u; break;
-        case O_BVS: take = fv ? 1u : 0u; break;
-        case O_BPL: take = (fn & 0x80) ? 0u : 1u; break;
-        default: take = (fn & 0x80) ? 1u : 0u; break;
-      }
-      PC = next;
-      if (take) {
-        const uint32_t tgt = (next + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF;
-        n += ((next ^ tgt) & 0xFF00) ? 2u : 1u;
-        PC = tgt;
-      }
-      kf = k0 + n;
-      instret++;
-      return true;
-    }
-    // stack and flow: RAM stack only
-    switch (op) {
-      case O_PHA: case O_PHP:
-        if (!(SP & 0x80)) return false;
-        ram[(SP & 0x7F) * E] = op == O_PHA ? A : (P() | 0x10u);
-        SP = (SP - 1) & 0xFF;
-        PC = next; kf = k0 + n; instret++;
-        return true;
-      case O_PLA: case O_PLP: {
-        const uint32_t sp1 = (SP + 1) & 0xFF;
-        if (!(sp1 & 0x80)) return false;
-        SP = sp1;
-        const uint32_t v = ram[(sp1 & 0x7F) * E];
-        if (op == O_PLA) { A = v; fn = fz = v; } else setP(v);
-        PC = next; kf = k0 + n; instret++;
-        return true;
-      }
-      case O_JSR: {
-        if (SP < 0x81) return false;
-        const uint32_t ret = (pc + 2) & 0xFFFF;
-        ram[(SP & 0x7F) * E] = ret >> 8;
-        ram[((SP - 1) & 0x7F) * E] = ret & 0xFF;
-        SP = (SP - 2) & 0xFF;
-        PC = ea; kf = k0 + n; instret++;
-        return true;
-      }
-      case O_RTS: {
-        const uint32_t s1 = (SP + 1) & 0xFF, s2 = (SP + 2) & 0xFF;
-        if (!(s1 & 0x80) || !(s2 & 0x80)) return false;
-        const uint32_t lo = ram[(s1 & 0x7F) * E], hi = ram[(s2 & 0x7F) * E];
-        SP = s2;
-        PC = ((lo | hi << 8) + 1) & 0xFFFF; kf = k0 + n; instret++;
-        return true;
-      }
-      case O_JMP: PC = ea; kf = k0 + n; instret++; return true;
-      default: break;
-    }
-    const uint32_t kA = k0 + n - 1;
-    const bool rmw = op == O_ASL || op == O_LSR || op == O_ROL || op == O_ROR || op == O_INC || op == O_DEC;
-    const bool store = op == O_STA || op == O_STX || op == O_STY;
-    wsync = 0;
-    vs_rise = 0;
-    // the single read site: operand of read instructions and read-modify-write
-    uint32_t v = 0;
-    if (mode == IMM) v = b1;
-    else if (mode == ACC) v = A;
-    else if (!store && mode != IMP) v = bus_read(ea, rmw ? kA - 2 : kA);
-    uint32_t r = v;
-    switch (op) {
-      case O_LDA: A = v; fn = fz = v; break;
-      case O_LDX: X = v; fn = fz = v; break;
-      case O_LDY: Y = v; fn = fz = v; break;
-      case O_STA: r = A; break;
-      case O_STX: r = X; break;
-      case O_STY: r = Y; break;
-      case O_ADC: adc(v); break;
-      case O_SBC: sbc(v); break;
-      case O_AND: A &= v; fn = fz = A; break;
-      case O_ORA: A |= v; fn = fz = A; break;
-      case O_EOR: A ^= v; fn = fz = A; break;
-      case O_CMP: cmp(A, v); break;
-      case O_CPX: cmp(X, v); break;
-      case O_CPY: cmp(Y, v); break;
-      case O_BIT: fn = v; fv = v & 0x40; fz = A & v; break;
-      case O_ASL: r = (v << 1) & 0xFF; fc = v >> 7; fn = fz = r; break;
-      case O_LSR: r = v >> 1; fc = v & 1; fn = fz = r; break;
-      case O_ROL: r = ((v << 1) | fc) & 0xFF; fc = v >> 7; fn = fz = r; break;
-      case O_ROR: r = (v >> 1) | (fc << 7); fc = v & 1; fn = fz = r; break;
-      case O_INC: r = (v + 1) & 0xFF; fn = fz = r; break;
-      case O_DEC: r = (v - 1) & 0xFF; fn = fz = r; break;
-      case O_INX: X = (X + 1) & 0xFF; fn = fz = X; break;
-      case O_INY: Y = (Y + 1) & 0xFF; fn = fz = Y; break;
-      case O_DEX: X = (X - 1) & 0xFF; fn = fz = X; break;
-      case O_DEY: Y = (Y - 1) & 0xFF; fn = fz = Y; break;
-      case O_TAX: X = A; fn = fz = X; break;
-      case O_TAY: Y = A; fn = fz = Y; break;
-      case O_TXA: A = X; fn = fz = A; break;
-      case O_TYA: A = Y; fn = fz = A; break;
-      case O_TSX: X = SP; fn = fz = X; break;
-      case O_TXS: SP = X; break;
-      case O_CLC: fc = 0; break;
-      case O_SEC: fc = 1; break;
-      case O_CLI: fdi &= ~0x04u; break;
-      case O_SEI: fdi |= 0x04u; break;
-      case O_CLV: fv = 0; break;
-      case O_CLD: fdi &= ~0x08u; break;
-      case O_SED: fdi |= 0x08u; break;
-      default: break;  // NOP
-    }
-    if (rmw && mode == ACC) A = r;
-    // the single write site: stores, and the two writes of read-modify-write
-    if (store || (rmw && mode != ACC)) {
-#pragma unroll 1
-      for (uint32_t wi = store ? 1u : 0u; wi < 2; ++wi) bus_write(ea, wi ? r : v, kA - 1 + wi);
-    }
-    PC = next;
+#undef ZPX_
+#undef ZPY_
+#undef ABX_
+#undef ABY_
+#undef XPG
+#undef NZ
+#undef RD_OPS
+#undef RMW_OPS
+#undef RMWM_OPS
+#undef BR
+#undef IMPL
+    PC &= 0xFFFF;
     uint32_t k = k0 + n;
-    if (wsync) k = ((k + 75u) / 76u) * 76u;
+    if (pend & IO_WSYNC) k = ((k + 75u) / 76u) * 76u;
     kf = k;
     instret++;
     return true;
   }
 
-  // ---- one instruction, general form (every case; used out of line) ----
-  __device__ __forceinline__ void exec_general() {
+  // ---- one instruction, general form (every case; run out of line) ----
+  __device__ void exec_general() {
     const uint32_t k0 = kf;
-    wsync = 0;
-    vs_rise = 0;
+    pend = 0;
     const uint32_t pc = PC;
-    const uint32_t off = pc & 0xFFF;
-    uint32_t w;
-    if ((pc & 0x1000) && off <= (scheme ? 0xFF3u : 0xFFDu)) {
-      w = romw[bank * 4096u + off];
-    } else {
-      // fetch byte by byte through the bus (code outside the cartridge or next to hotspots)
-      const uint32_t op0 = rd(pc, k0);
-      const uint32_t info = romw_info_of(op0);
-      const uint32_t mode = info & 0xF;
-      const uint32_t b1 = (mode >= IMM) ? rd(pc + 1, k0) : 0u;
-      const uint32_t b2 = (mode >= ABS && mode <= IND) ? rd(pc + 2, k0) : 0u;
-      w = op0 | b1 << 8 | b2 << 16 | info << 24;
-    }
-    const uint32_t op = dec_op[w & 0xFF];
-    const uint32_t mode = romw_mode(w);
-    uint32_t n = romw_cycles(w);
+    const uint32_t opcode = rd(pc, k0);
+    const uint32_t op = dec_op[opcode];
+    const uint32_t info = dec_op[256 + opcode];
+    const uint32_t mode = info & 0xF;
+    uint32_t n = (info >> 4) & 7;
     if (op == O_JAM) { jam = 1; status |= ST_ILLEGAL; return; }
-    const uint32_t b1 = (w >> 8) & 0xFF, b2 = (w >> 16) & 0xFF;
-    uint32_t ea = 0, cross = 0;
+    uint32_t b1 = 0, b2 = 0, ea = 0, cross = 0;
+    if (mode >= IMM) b1 = rd(pc + 1, k0);
+    if (mode >= ABS && mode <= IND) b2 = rd(pc + 2, k0);
     switch (mode) {
       case IMP: case ACC: PC = (pc + 1) & 0xFFFF; break;
       case IMM: PC = (pc + 2) & 0xFFFF; break;
@@ -672,18 +701,18 @@ struct FastConsole {
       case ZPX: ea = (b1 + X) & 0xFF; PC = (pc + 2) & 0xFFFF; break;
       case ZPY: ea = (b1 + Y) & 0xFF; PC = (pc + 2) & 0xFFFF; break;
       case ABS: ea = b1 | b2 << 8; PC = (pc + 3) & 0xFFFF; break;
-      case ABX: { uint32_t b = b1 | b2 << 8; ea = (b + X) & 0xFFFF; cross = (b ^ ea) >> 8; PC = (pc + 3) & 0xFFFF; break; }
-      case ABY: { uint32_t b = b1 | b2 << 8; ea = (b + Y) & 0xFFFF; cross = (b ^ ea) >> 8; PC = (pc + 3) & 0xFFFF; break; }
-      case IND: { uint32_t p = b1 | b2 << 8;
-                  uint32_t lo = rd(p, k0), hi = rd((p & 0xFF00) | ((p + 1) & 0xFF), k0);
+      case ABX: { const uint32_t b = b1 | b2 << 8; ea = (b + X) & 0xFFFF; cross = (b ^ ea) >> 8; PC = (pc + 3) & 0xFFFF; break; }
+      case ABY: { const uint32_t b = b1 | b2 << 8; ea = (b + Y) & 0xFFFF; cross = (b ^ ea) >> 8; PC = (pc + 3) & 0xFFFF; break; }
+      case IND: { const uint32_t p = b1 | b2 << 8;
+                  const uint32_t lo = rd(p, k0), hi = rd((p & 0xFF00) | ((p + 1) & 0xFF), k0);
                   ea = lo | hi << 8; PC = (pc + 3) & 0xFFFF; break; }
-      case IZX: { uint32_t z = (b1 + X) & 0xFF; uint32_t lo = rd(z, k0), hi = rd((z + 1) & 0xFF, k0);
+      case IZX: { const uint32_t z = (b1 + X) & 0xFF; const uint32_t lo = rd(z, k0), hi = rd((z + 1) & 0xFF, k0);
                   ea = lo | hi << 8; PC = (pc + 2) & 0xFFFF; break; }
-      case IZY: { uint32_t lo = rd(b1, k0), hi = rd((b1 + 1) & 0xFF, k0); uint32_t b = lo | hi << 8;
+      case IZY: { const uint32_t lo = rd(b1, k0), hi = rd((b1 + 1) & 0xFF, k0); const uint32_t b = lo | hi << 8;
                   ea = (b + Y) & 0xFFFF; cross = (b ^ ea) >> 8; PC = (pc + 2) & 0xFFFF; break; }
-      default: PC = (pc + 2) & 0xFFFF; ea = (PC + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF; break;  // REL
+      default: PC = (pc + 2) & 0xFFFF; ea = (PC + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF; break;
     }
-    if (cross && (w >> 31)) n++;
+    if (cross && (info >> 7)) n++;
     instret++;
     if (mode == REL) {
       uint32_t take;
@@ -697,10 +726,7 @@ struct FastConsole {
         case O_BPL: take = (fn & 0x80) ? 0u : 1u; break;
         default: take = (fn & 0x80) ? 1u : 0u; break;
       }
-      if (take) {
-        n += ((PC ^ ea) & 0xFF00) ? 2u : 1u;
-        PC = ea;
-      }
+      if (take) { n += ((PC ^ ea) & 0xFF00) ? 2u : 1u; PC = ea; }
       kf = k0 + n;
       return;
     }
@@ -720,19 +746,18 @@ struct FastConsole {
       case O_CMP: cmp(A, mode == IMM ? b1 : rd(ea, kA)); break;
       case O_CPX: cmp(X, mode == IMM ? b1 : rd(ea, kA)); break;
       case O_CPY: cmp(Y, mode == IMM ? b1 : rd(ea, kA)); break;
-      case O_BIT: { uint32_t v = rd(ea, kA); fn = v; fv = v & 0x40; fz = A & v; break; }
+      case O_BIT: { const uint32_t v = rd(ea, kA); fn = v; fv = v & 0x40; fz = A & v; break; }
       case O_ASL: case O_LSR: case O_ROL: case O_ROR: case O_INC: case O_DEC: {
         const uint32_t old = mode == ACC ? A : rd(ea, kA - 2);
         uint32_t r;
         switch (op) {
-          case O_ASL: r = (old << 1) & 0xFF; fc = old >> 7; break;
-          case O_LSR: r = old >> 1; fc = old & 1; break;
-          case O_ROL: r = ((old << 1) | fc) & 0xFF; fc = old >> 7; break;
-          case O_ROR: r = (old >> 1) | (fc << 7); fc = old & 1; break;
-          case O_INC: r = (old + 1) & 0xFF; break;
-          default: r = (old - 1) & 0xFF; break;
+          case O_ASL: r = asl(old); break;
+          case O_LSR: r = lsr(old); break;
+          case O_ROL: r = rol(old); break;
+          case O_ROR: r = ror(old); break;
+          case O_INC: r = inc(old); break;
+          default: r = dec(old); break;
         }
-        fn = fz = r;
         if (mode == ACC) A = r;
         else { wr(ea, old, kA - 1); wr(ea, r, kA); }
         break;
@@ -754,52 +779,82 @@ struct FastConsole {
       case O_CLV: fv = 0; break;
       case O_CLD: fdi &= ~0x08u; break;
       case O_SED: fdi |= 0x08u; break;
-      case O_PHA: push(A, kA); break;
-      case O_PHP: push(P() | 0x10u, kA); break;
-      case O_PLA: A = pull(kA); fn = fz = A; break;
-      case O_PLP: setP(pull(kA)); break;
+      case O_PHA: wr(0x100u | SP, A, kA); SP = (SP - 1) & 0xFF; break;
+      case O_PHP: wr(0x100u | SP, P() | 0x10u, kA); SP = (SP - 1) & 0xFF; break;
+      case O_PLA: SP = (SP + 1) & 0xFF; A = rd(0x100u | SP, kA); fn = fz = A; break;
+      case O_PLP: SP = (SP + 1) & 0xFF; setP(rd(0x100u | SP, kA)); break;
       case O_JMP: PC = ea; break;
-      case O_JSR: { uint32_t ret = (pc + 2) & 0xFFFF; push(ret >> 8, kA); push(ret & 0xFF, kA); PC = ea; break; }
-      case O_RTS: { uint32_t lo = pull(kA); uint32_t hi = pull(kA); PC = ((lo | hi << 8) + 1) & 0xFFFF; break; }
-      case O_RTI: { setP(pull(kA)); uint32_t lo = pull(kA); uint32_t hi = pull(kA); PC = lo | hi << 8; break; }
+      case O_JSR: {
+        const uint32_t ret = (pc + 2) & 0xFFFF;
+        wr(0x100u | SP, ret >> 8, kA); SP = (SP - 1) & 0xFF;
+        wr(0x100u | SP, ret & 0xFF, kA); SP = (SP - 1) & 0xFF;
+        PC = ea;
+        break;
+      }
+      case O_RTS: {
+        SP = (SP + 1) & 0xFF; const uint32_t lo = rd(0x100u | SP, kA);
+        SP = (SP + 1) & 0xFF; const uint32_t hi = rd(0x100u | SP, kA);
+        PC = ((lo | hi << 8) + 1) & 0xFFFF;
+        break;
+      }
+      case O_RTI: {
+        SP = (SP + 1) & 0xFF; setP(rd(0x100u | SP, kA));
+        SP = (SP + 1) & 0xFF; const uint32_t lo = rd(0x100u | SP, kA);
+        SP = (SP + 1) & 0xFF; const uint32_t hi = rd(0x100u | SP, kA);
+        PC = lo | hi << 8;
+        break;
+      }
       case O_BRK: {
-        uint32_t ret = (pc + 2) & 0xFFFF;
-        push(ret >> 8, kA); push(ret & 0xFF, kA); push(P() | 0x10u, kA);
+        const uint32_t ret = (pc + 2) & 0xFFFF;
+        wr(0x100u | SP, ret >> 8, kA); SP = (SP - 1) & 0xFF;
+        wr(0x100u | SP, ret & 0xFF, kA); SP = (SP - 1) & 0xFF;
+        wr(0x100u | SP, P() | 0x10u, kA); SP = (SP - 1) & 0xFF;
         fdi |= 0x04u;
-        uint32_t lo = rd(0x1FFE, kA), hi = rd(0x1FFF, kA);
+        const uint32_t lo = rd(0x1FFE, kA), hi = rd(0x1FFF, kA);
         PC = lo | hi << 8;
         break;
       }
       default: break;  // NOP
     }
     uint32_t k = k0 + n;
-    if (wsync) k = ((k + 75u) / 76u) * 76u;
+    if (pend & IO_WSYNC) k = ((k + 75u) / 76u) * 76u;
     kf = k;
   }
-  // mode/cycles/penalty of an opcode for the byte-wise fetch path
-  __device__ __forceinline__ uint32_t romw_info_of(uint32_t opcode) const { return dec_op[256 + opcode]; }
 
+  // One frame.  Lanes of a warp issue in emulated-cycle order: each round only
+  // the lanes at the warp's smallest cycle count execute an instruction, so
+  // lanes that ran a shorter path wait, and the warp realigns whenever the
+  // programs meet again in time (every WSYNC).  The lane with the smallest
+  // count always advances (every instruction takes at least 2 cycles, and a
+  // frame ends after at most 400 lines), so the loop ends.
   __device__ __forceinline__ uint32_t run_frame() {
-    uint32_t next_rel;
-    vs_rise = 0;
-    for (;;) {
-      if (jam) { next_rel = kf / 76u; break; }
-      if (!exec()) fc_exec_general(this);
-      if (jam) { next_rel = kf / 76u; break; }
-      if (vs_rise) { next_rel = vs_kf / 76u; break; }
-      if (kf >= 76u * CAP_LINES) { status |= ST_FRAME_CAP; next_rel = kf / 76u; break; }
+    uint32_t next_rel = 0;
+    vs_kf = ~0u;
+    bool active = true;
+    while (__any_sync(wmask, active)) {
+      const uint32_t mine = active ? kf : 0xFFFFFFFFu;
+      const uint32_t lead = __reduce_min_sync(wmask, mine);
+      if (active && kf == lead) {
+        if (jam) {
+          next_rel = kf / 76u;
+          active = false;
+        } else {
+          if (!exec()) fc_exec_general(this);
+          if (jam) { next_rel = kf / 76u; active = false; }
+          else if (vs_kf != ~0u) { next_rel = vs_kf / 76u; active = false; }
+          else if (kf >= 76u * CAP_LINES) { status |= ST_FRAME_CAP; next_rel = kf / 76u; active = false; }
+        }
+      }
     }
-    cx_eval(3u * kf);
-    L0 += next_rel;
+    fc_frame_end(io, kf, next_rel);
     kf -= 76u * next_rel;
-    ceval -= 228u * next_rel;
     frame_no++;
     return next_rel;
   }
 };
 
-// Out-of-line general instruction: runs on a copy of the register state (the
-// caller's console stays in registers; only this rare path touches memory).
+// Out-of-line general instruction on a copy of the register state (the
+// caller's console stays in registers).
 __device__ __noinline__ void fc_exec_general_impl(FastConsole *c) { c->exec_general(); }
 __device__ __forceinline__ void fc_exec_general(FastConsole *self) {
   FastConsole tmp = *self;
