@@ -49,7 +49,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--form", default="batched", choices=["plain", "batched"])
-    p.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 5])
+    p.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5])
+    p.add_argument("--serve-seconds", type=float, default=60.0)
+    p.add_argument("--serve-clients", type=int, default=64)
     p.add_argument("--n-envs", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -228,10 +230,73 @@ def reference_arm(args, w, ws, rank):
     }), flush=True)
 
 
+def serve_bench(args, ws, rank, local):
+    """Serving loop: N native client threads (closed loop, Exp(2 ms) think
+    time) open sessions of U{1..2048} envs on the 32 banked cartridges, step
+    them (stacks, rewards and dones back to pinned host memory) and close
+    them; admission under a 40 GB device budget.  value = aggregate emulated
+    frames/s over the run; p50/p99 = request latency (submit to outputs in
+    place)."""
+    import torch
+
+    from paper_1907_08467_gb300 import synth
+    from paper_1907_08467_gb300.server import AtariServer
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle has no serving loop; the serving "
+                              "workload is measured against the plain and batched GPU paths"}), flush=True)
+        return
+    torch.cuda.set_device(local)
+    w = synth.workload(3, n_envs=32)
+    clients, max_envs = args.serve_clients, 2048
+    srv = AtariServer.from_roms(w.roms, budget_bytes=40 << 30, max_slots=clients * max_envs, sticky=True,
+                                seed=w.seed)
+    warm = srv.loadgen(n_clients=clients, seconds=max(1.0, float(args.warmup)), think_mean_ms=2.0, min_envs=1,
+                       max_envs=max_envs, session_steps_mean=100, seed=1000 + rank, want_obs=True)
+    clocks = ClockSampler(local)
+    barrier(ws)
+    l0 = srv.stats()["launches"]
+    clocks.start()
+    r = srv.loadgen(n_clients=clients, seconds=args.serve_seconds, think_mean_ms=2.0, min_envs=1,
+                    max_envs=max_envs, session_steps_mean=100, seed=1 + rank, want_obs=True)
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    value = allreduce_sum(r["frames"], ws) / allreduce_max(r["seconds"], ws)
+    if rank == 0:
+        reqs = max(1, r["requests"])
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": r["requests"],
+            "warmup": warm["requests"], "ms_per_step": r["mean_ms"], "p50_step_ms": r["p50_ms"],
+            "p99_step_ms": r["p99_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic (seeded cartridges, client actions and arrivals)",
+            "config": {"workload": f"serving: {clients} clients, sessions U{{1..{max_envs}}} envs on 32 banked "
+                                   "4k/f8/f6 roms, sticky, closed loop Exp(2 ms) think, geometric sessions "
+                                   "(mean 100 steps), 40 GB budget",
+                       "seconds": r["seconds"], "budget_bytes": st["budget_bytes"], "capacity": st["capacity"],
+                       "per_env_bytes": st["per_env_bytes"], "parallelism": f"replicas x{ws}",
+                       "l2": "inputs (slots of all admitted sessions) far larger than L2"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": r["h2d_bytes"] // reqs,
+                    "d2h_bytes_per_step": r["d2h_bytes"] // reqs},
+            "serving": {"requests": r["requests"], "sessions": r["sessions"], "ticks": r["ticks"],
+                        "mean_tick_envs": r["mean_tick_envs"], "latency_ms": {"p50": r["p50_ms"], "p99": r["p99_ms"],
+                                                                              "max": r["max_ms"], "mean": r["mean_ms"]},
+                        "admission_wait_ms": {"p50": r["admit_p50_ms"], "p99": r["admit_p99_ms"]}},
+            "gpu_launches": int(st["launches"] - l0), "clocks": clk, "roofline": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     from paper_1907_08467_gb300 import synth
+    if args.config == 4:
+        serve_bench(args, ws, rank, local)
+        return
     w = synth.workload(args.config, n_envs=args.n_envs)
     if args.impl == "reference":
         reference_arm(args, w, ws, rank)

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/atari_gpu.h"
+#include "env_internal.h"
 #include "device_machine.cuh"
 #include "render.cuh"
 #include "batched.cuh"
@@ -574,6 +575,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
   a.grp_start = E->d_grp + E->n_groups;
   a.grp_count = E->d_grp + 2 * E->n_groups;
   a.perm = E->d_grp + 3 * E->n_groups;
+  a.opos = nullptr;
   a.queue = E->d_queue;
   a.n_groups = E->n_groups;
   a.lanes = E->lanes;
@@ -886,7 +888,7 @@ int launch_batched(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
   if (c.output_mode == ATARI_OUT_STACK) {
     ProfScope p(E, ATARI_PROF_FUSED, s);
     k_raster_preprocess<<<E->n, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma, E->d_ring,
-                                                                E->d_head, E->d_done, d_obs, E->n, c.log_cap, E->wpf);
+                                                                E->d_head, E->d_done, d_obs, E->n, c.log_cap, E->wpf, nullptr, nullptr);
   } else if (d_obs) {
     ProfScope p(E, ATARI_PROF_RASTER, s);
     k_raster<<<(unsigned)((E->n + 3) / 4), 128, 0, s>>>(E->d_log, E->d_snap, E->d_meta, d_obs, (size_t)210 * 160,
@@ -978,7 +980,7 @@ int autotune(atari_env *E) {
         for (int rep = 0; rep < 2; ++rep) {
           cudaEventRecord(e0);
           k_raster_preprocess<<<E->n, 64 * wpf, fused_smem()>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma, E->d_ring,
-                                                               E->d_head, E->d_done, nullptr, E->n, E->cfg.log_cap, wpf);
+                                                               E->d_head, E->d_done, nullptr, E->n, E->cfg.log_cap, wpf, nullptr, nullptr);
           cudaEventRecord(e1);
           cudaEventSynchronize(e1);
           cudaEventElapsedTime(&t, e0, e1);
@@ -1374,3 +1376,79 @@ extern "C" int atari_step_noalloc(const uint8_t *rom, size_t rom_size, atari_rom
   }
   return 0;
 }
+
+// ---------------------------------------------------------------------------
+// Serving ticks: the env is a pool of slots; each tick steps the slots of the
+// sessions whose requests it carries (see env_internal.h).
+
+namespace {
+
+// Slots that start a new session: env fields cleared, key and cartridge set,
+// episode 0 from the start-state cache, empty stack.  One block per slot.
+__global__ void k_serve_init(uint8_t *state, const uint8_t *cache, const uint32_t *info, int32_t *env_rom,
+                             uint32_t *env_key, uint8_t *ring, uint8_t *head, const int32_t *init, int n_init,
+                             int n_cache, uint64_t seed) {
+  const int k = blockIdx.x;
+  if (k >= n_init) return;
+  const int slot = init[k];
+  const uint32_t rom = (uint32_t)init[n_init + k];
+  const uint32_t key = (uint32_t)init[2 * n_init + k];
+  if (threadIdx.x == 0) {
+    uint8_t *st = state + (size_t)slot * 256;
+    for (int b = 0x60; b < 0x80; ++b) st[b] = 0;
+    Console<GlobalMem>::st32(st + S::ENV_KEY, key);
+    st[S::ROM] = rom & 0xFF;
+    st[S::ROM + 1] = rom >> 8;
+    reset_from_cache(st, cache, info, rom, (uint32_t)n_cache, seed, key, 0u);
+    env_rom[slot] = (int32_t)rom;
+    env_key[slot] = key;
+    head[slot] = 0;
+  }
+  uint4 *p = reinterpret_cast<uint4 *>(ring + (size_t)slot * 4 * 7056);
+  for (int q = threadIdx.x; q < 4 * 7056 / 16; q += blockDim.x) p[q] = make_uint4(0, 0, 0, 0);
+}
+
+}  // namespace
+
+namespace atari_internal {
+
+int env_slots(const atari_env *E) { return E ? E->n : 0; }
+int env_device(const atari_env *E) { return E ? E->device : 0; }
+int env_n_roms(const atari_env *E) { return E ? E->n_roms : 0; }
+int env_frameskip(const atari_env *E) { return E ? E->cfg.frameskip : 0; }
+void env_shape(const atari_env *E, int *lanes, int *warps) {
+  *lanes = E->lanes;
+  *warps = E->warps;
+}
+int set_error(int code, const std::string &msg) { return fail(code, msg); }
+
+int serve_tick(atari_env *E, const ServeTick &t, cudaStream_t s) {
+  if (!E || E->cfg.form != ATARI_FORM_BATCHED || E->cfg.output_mode != ATARI_OUT_STACK)
+    return fail(ATARI_EINVAL, "serving needs a batched env with stack output");
+  if (t.n_active <= 0) return 0;
+  const atari_config &c = E->cfg;
+  if (t.n_init > 0) {
+    k_serve_init<<<t.n_init, 128, 0, s>>>(E->d_state, E->d_cache, E->d_info, E->d_env_rom, E->d_env_key, E->d_ring,
+                                          E->d_head, t.d_init, t.n_init, c.n_cache, c.seed);
+    CUDA_TRY(cudaGetLastError());
+  }
+  BatchArgs a = batch_args(E, t.d_actions, t.d_rew, t.d_done);
+  a.grp_rom = t.d_blob;
+  a.grp_start = t.d_blob + t.n_groups;
+  a.grp_count = t.d_blob + 2 * t.n_groups;
+  a.perm = t.d_blob + 3 * t.n_groups;
+  a.opos = a.perm + t.n_active;
+  a.queue = t.d_queue;
+  a.n_groups = t.n_groups;
+  CUDA_TRY(cudaMemsetAsync(t.d_queue, 0, sizeof(int), s));
+  const int grid = std::max(1, std::min(t.n_groups, E->max_blocks));
+  k_interp_batched<<<grid, E->warps * 32, interp_smem(E), s>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  k_raster_preprocess<<<t.n_active, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma,
+                                                                   E->d_ring, E->d_head, E->d_done, t.d_obs,
+                                                                   t.n_active, c.log_cap, E->wpf, a.perm, a.opos);
+  CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace atari_internal

@@ -38,6 +38,7 @@ struct BatchArgs {
   uint32_t *meta;
   uint32_t *counters;
   const int32_t *grp_rom, *grp_start, *grp_count, *perm;
+  const int32_t *opos;       // null, or the packed action/output position of each work-list entry
   int *queue;
   int n_groups, lanes, E, romw_words;
   int frameskip, sticky, n_cache, log_cap, first_slot;
@@ -60,13 +61,14 @@ __device__ __forceinline__ void fast_reset_from_cache(uint8_t *st, const uint8_t
   *reinterpret_cast<uint32_t *>(st + S::EPISODE) = episode;
 }
 
-__device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i, const BatchArgs &a,
+// Env slot i; o = where its action is read and its reward and done written.
+__device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i, int o, const BatchArgs &a,
                                               uint32_t rom, uint32_t score, uint32_t gameover) {
   const uint32_t *ew = reinterpret_cast<const uint32_t *>(st + S::EPISODE);
   uint32_t episode = ew[0], step_no = ew[1], env_key = ew[2], env_status = ew[3];
   uint32_t last = st[S::LAST_ACTION];
   uint32_t score_prev = st[S::SCORE_PREV];
-  uint32_t action = a.actions[i];
+  uint32_t action = a.actions[o];
   if (action >= 18) { env_status |= ST_BAD_ACTION; action = 0; }
   int32_t reward = 0;
   uint32_t log_total = 0;
@@ -104,8 +106,8 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
   const uint32_t done = (m.ram[gameover * m.E] != 0 || m.jam) ? 1u : 0u;
   a.rew_int[i] = reward;
   a.done_int[i] = (uint8_t)done;
-  if (a.rew_out) a.rew_out[i] = reward;
-  if (a.done_out) a.done_out[i] = (uint8_t)done;
+  if (a.rew_out) a.rew_out[o] = reward;
+  if (a.done_out) a.done_out[o] = (uint8_t)done;
   if (a.counters) {
     a.counters[2 * i] = m.instret;
     a.counters[2 * i + 1] = log_total;
@@ -154,7 +156,9 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
     if (runs) {
       const int j = jj;
       {
-        const int i = a.perm[a.grp_start[g] + j];
+        const int p = a.grp_start[g] + j;
+        const int i = a.perm[p];
+        const int o = a.opos ? a.opos[p] : i;
         uint8_t *st = a.state + (size_t)i * 256;
         const uint32_t inf = a.info[rom];
         FastConsole m;
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
         m.scheme = inf & 0xFF;
         m.wmask = wmask;
         m.load(st);
-        fast_step_env(m, st, i, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
+        fast_step_env(m, st, i, o, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
       }
     }
   }
@@ -225,14 +229,17 @@ __device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uin
 __global__ void __launch_bounds__(256) k_raster_preprocess(const uint32_t *log, const uint8_t *snap, const uint32_t *meta,
                                                            const uint8_t *luma_g, uint8_t *ring, uint8_t *head,
                                                            const uint8_t *done, uint8_t *obs, int n, int log_cap,
-                                                           int warps_per_frame) {
+                                                           int warps_per_frame, const int32_t *perm,
+                                                           const int32_t *opos) {
   extern __shared__ __align__(16) uint8_t sm[];
   uint8_t *fa = sm;                        // frame F-1, later the luma maximum
   uint8_t *fb = sm + FRAME_H * FRAME_W;    // frame F
   uint8_t *luma = fb + FRAME_H * FRAME_W;
   uint8_t *plane = luma + 128;
-  const int i = blockIdx.x;
-  if (i >= n) return;
+  if ((int)blockIdx.x >= n) return;
+  // block b serves env slot perm[b] and writes its stack at position opos[b]
+  const int i = perm ? perm[blockIdx.x] : (int)blockIdx.x;
+  const int o = opos ? opos[blockIdx.x] : i;
   const int warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < 128; t += blockDim.x) luma[t] = luma_g[t];
   if (warp < 2 * warps_per_frame) {
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(256) k_raster_preprocess(const uint32_t *log, 
   uint8_t *rg = ring + (size_t)i * 4 * 7056;
   const uint32_t *pl32 = reinterpret_cast<const uint32_t *>(plane);
   if (obs) {
-    uint8_t *ob = obs + (size_t)i * 4 * 7056;
+    uint8_t *ob = obs + (size_t)o * 4 * 7056;
     for (int s = 0; s < 3; ++s) {
       const uint4 *src = reinterpret_cast<const uint4 *>(rg + ((h + 1 + s) & 3) * 7056);
       uint4 *dst = reinterpret_cast<uint4 *>(ob + s * 7056);

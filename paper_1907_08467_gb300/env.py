@@ -39,7 +39,9 @@ EXPORTS = ["atari_default_config", "atari_env_create", "atari_env_reset", "atari
            "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
            "atari_env_footprint", "atari_env_destroy", "atari_last_error", "atari_env_profile",
            "atari_env_profile_read", "atari_env_launch_shape", "atari_step_noalloc", "atari_env_policy",
-           "atari_env_rollout"]
+           "atari_env_rollout", "atari_server_default_config", "atari_server_footprint", "atari_server_create",
+           "atari_server_open", "atari_server_step", "atari_server_close", "atari_server_get_stats",
+           "atari_server_destroy", "atari_server_loadgen"]
 PROF_SLOTS = 8
 PROF_NAMES = ["interpreter", "rasteriser", "preprocess", "fused_raster_preprocess", "copy", "policy", "s6", "s7"]
 
@@ -78,6 +80,8 @@ def load_library(path: str | None = None):
         L.atari_step_noalloc.restype = C.c_int
         L.atari_env_policy.argtypes = [P, P, P, P, P, P]
         L.atari_env_rollout.argtypes = [P, P, C.c_int, P, P, P, P, P, P, C.c_int, C.c_int, P]
+        from . import server as _srv
+        _srv.declare(L)
         for name in ("atari_env_create", "atari_env_reset", "atari_env_step", "atari_env_step_host",
                      "atari_env_status", "atari_env_get_state", "atari_env_set_state",
                      "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",

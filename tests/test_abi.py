@@ -87,3 +87,45 @@ def test_no_device_reports_cuda_error_instead_of_crashing(lib):
         pytest.skip("a GPU is present")
     rc, out = _create(lib, [b"\xea" * 4096], [4096])
     assert rc in (-5, -12) and not out.value
+
+
+def test_server_footprint_and_host_validation(lib):
+    """Serving: footprint = env footprint + per-tick buffers for each tick in
+    flight; create refuses a plain-form config and a budget below one env
+    slot before touching the device."""
+    from paper_1907_08467_gb300 import server as S
+    c = E.make_config(form=E.FORM_BATCHED)
+    s2 = S.server_config(inflight=2)
+    s3 = S.server_config(inflight=3)
+    f = lambda slots, tick, sc: lib.atari_server_footprint(slots, tick, 32, C.byref(c), C.byref(sc))
+    env_per = lib.atari_env_footprint(2000, 32, C.byref(c)) - lib.atari_env_footprint(1000, 32, C.byref(c))
+    assert f(2000, 0, s2) - f(1000, 0, s2) == env_per
+    tick_per = (f(1000, 2000, s2) - f(1000, 1000, s2)) / 1000 / 2
+    assert 4 * 7056 <= tick_per < 4 * 7056 + 64      # packed stack + actions/rewards/dones/work list
+    assert f(1000, 1000, s3) > f(1000, 1000, s2)
+    roms = [bytes(4096)]
+    buf = [C.create_string_buffer(r, len(r)) for r in roms]
+    rp = (C.c_void_p * 1)(*[C.cast(b, C.c_void_p) for b in buf])
+    sz = (C.c_size_t * 1)(4096)
+    meta = (E._Meta * 1)(E._Meta(0x80, 0x81))
+    luma = (C.c_uint8 * 128)()
+    out = C.c_void_p()
+    small = S.server_config(budget_bytes=100 << 10)   # below the cartridge images plus one slot
+    assert lib.atari_server_create(rp, sz, meta, 1, C.byref(c), luma, C.byref(small), C.byref(out)) == -12
+    assert b"budget" in lib.atari_last_error()
+    plain = E.make_config(form=E.FORM_PLAIN)
+    assert lib.atari_server_create(rp, sz, meta, 1, C.byref(plain), luma, C.byref(s2), C.byref(out)) == -22
+    bad = S.server_config(inflight=9)
+    assert lib.atari_server_create(rp, sz, meta, 1, C.byref(c), luma, C.byref(bad), C.byref(out)) == -22
+    assert not out.value
+
+
+def test_server_binding_marshals_to_the_library():
+    """AtariServer passes cartridges, luma table and limits through the C ABI:
+    a budget below one env slot comes back as the library's ENOMEM."""
+    from paper_1907_08467_gb300 import synth
+    from paper_1907_08467_gb300.server import AtariServer, ServerError
+    w = synth.workload(3, n_envs=32)
+    with pytest.raises(ServerError) as e:
+        AtariServer.from_roms(w.roms[:3], budget_bytes=100 << 10, sticky=True)
+    assert e.value.rc == -12 and "budget" in str(e.value)
