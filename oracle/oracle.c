@@ -820,6 +820,7 @@ static void put16(uint8_t *o, uint16_t v) { o[0] = (uint8_t)v; o[1] = (uint8_t)(
 static void put32(uint8_t *o, uint32_t v) { for (int i = 0; i < 4; i++) o[i] = (uint8_t)(v >> (8 * i)); }
 static void put64(uint8_t *o, uint64_t v) { for (int i = 0; i < 8; i++) o[i] = (uint8_t)(v >> (8 * i)); }
 static uint16_t get16(const uint8_t *o) { return (uint16_t)(o[0] | o[1] << 8); }
+static uint32_t get32(const uint8_t *o) { return (uint32_t)o[0] | (uint32_t)o[1] << 8 | (uint32_t)o[2] << 16 | (uint32_t)o[3] << 24; }
 static uint64_t get64(const uint8_t *o) { uint64_t v = 0; for (int i = 7; i >= 0; i--) v = v << 8 | o[i]; return v; }
 
 static void pack_machine(const orc_machine *m, uint8_t *o) {
@@ -848,7 +849,8 @@ static void pack_machine(const orc_machine *m, uint8_t *o) {
 
 static void unpack_machine(orc_machine *m, const uint8_t *o) {
     m->a = o[0x00]; m->x = o[0x01]; m->y = o[0x02]; m->sp = o[0x03]; m->p = o[0x04];
-    m->bank = o[0x05]; m->pc = get16(o + 0x06);
+    /* the cartridge latches only its own bank bits: one for F8, two for F6 */
+    m->bank = (uint8_t)(o[0x05] & (m->scheme == 2 ? 3u : m->scheme == 1 ? 1u : 0u)); m->pc = get16(o + 0x06);
     m->k = get64(o + 0x08);
     m->tim_cw = get64(o + 0x10);
     m->tim_v = o[0x18]; m->tim_shift = o[0x19]; m->swcha_out = o[0x1A]; m->swacnt = o[0x1B];
@@ -1150,6 +1152,22 @@ int orc_envs_step(orc_envs *e, const uint8_t *actions, uint8_t *obs, int32_t *re
     for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, step_worker, &jobs[t]);
     for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
     return 0;
+}
+
+/* Inverse of orc_envs_get_state for the machine and env fields; each env
+ * keeps its cartridge (the state's cartridge field is not read). */
+void orc_envs_set_state(orc_envs *e, const uint8_t *in) {
+    for (int i = 0; i < e->n_envs; i++) {
+        orc_env *v = &e->env[i];
+        const uint8_t *o = in + (size_t)ORC_STATE_BYTES * i;
+        unpack_machine(&v->m, o);
+        v->episode = get32(o + 0x60);
+        v->step_no = get32(o + 0x64);
+        v->env_key = get32(o + 0x68);
+        v->status = get32(o + 0x6C);
+        v->last_action = o[0x70];
+        v->score_prev = o[0x71];
+    }
 }
 
 void orc_envs_get_state(const orc_envs *e, uint8_t *out) {

@@ -85,6 +85,7 @@ void orc_envs_free(orc_envs *e);
 int orc_envs_step(orc_envs *e, const uint8_t *actions, uint8_t *obs, int32_t *rewards,
                   uint8_t *dones, int n_threads);
 void orc_envs_get_state(const orc_envs *e, uint8_t *out /* n*256 */);
+void orc_envs_set_state(orc_envs *e, const uint8_t *in /* n*256 */);
 void orc_envs_get_frames(const orc_envs *e, uint8_t *out /* n*2*210*160: frames F-1, F */);
 void orc_envs_get_cache(const orc_envs *e, uint8_t *out /* n_roms*n_cache*256 */);
 void orc_envs_reset(orc_envs *e, const uint8_t *mask /* NULL: all */);

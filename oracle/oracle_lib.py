@@ -69,6 +69,7 @@ def lib():
             L.orc_envs_free.argtypes = [P]
             L.orc_envs_step.argtypes = [P, P, P, P, P, C.c_int]
             L.orc_envs_get_state.argtypes = [P, P]
+            L.orc_envs_set_state.argtypes = [P, P]
             L.orc_envs_get_frames.argtypes = [P, P]
             L.orc_envs_get_cache.argtypes = [P, P]
             L.orc_envs_reset.argtypes = [P, P]
@@ -231,6 +232,11 @@ class OracleEnvs:
         o = np.zeros((self.n_envs, STATE_BYTES), dtype=np.uint8)
         lib().orc_envs_get_state(self.h, _ptr(o))
         return o
+
+    def set_state(self, st: np.ndarray):
+        st = np.ascontiguousarray(st, dtype=np.uint8)
+        assert st.shape == (self.n_envs, STATE_BYTES)
+        lib().orc_envs_set_state(self.h, _ptr(st))
 
     def frames(self) -> np.ndarray:
         o = np.zeros((self.n_envs, 2, 210, 160), dtype=np.uint8)

@@ -166,8 +166,8 @@ __global__ void k_cache_run(uint8_t *work, uint8_t *snaps, const uint8_t *roms, 
   m.log.rec = nullptr;
   m.log.n = 0;
   m.log.cap = 0;
-  m.load(st);
   m.scheme = rom_info(info, r).scheme;
+  m.load(st);
   for (int f = 0; f < startup; ++f) {
     m.apply_action(0);
     m.run_frame();
@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(128) k_interp_plain(StepArgs a) {
   m.mem.ram = st + S::RAM;
   m.mem.rom = a.roms + (size_t)rom * ROM_SLOT;
   m.dec = dec;
-  m.load(st);
   m.scheme = ri.scheme;
+  m.load(st);
   step_env(m, st, i, a, ri);
   // machine part written before a possible reset overwrote it: store first
   // when not done; reset_from_cache already wrote the whole machine part
@@ -1285,8 +1285,8 @@ __global__ void __launch_bounds__(128) k_interp_noalloc(StepArgs a) {
   m.mem.ram = st + S::RAM;
   m.mem.rom = a.roms;
   m.dec = dec;
-  m.load(st);
   m.scheme = ri.scheme;
+  m.load(st);
   step_env(m, st, i, a, ri);
   if (!a.done_int[i]) m.store(st);
 }

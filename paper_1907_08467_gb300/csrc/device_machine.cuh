@@ -247,7 +247,9 @@ struct Console {
 
   // ---- canonical state I/O (machine part) ----
   __device__ void load(const uint8_t *s) {
-    A = s[S::A]; X = s[S::X]; Y = s[S::Y]; SP = s[S::SP]; P = s[S::P]; bank = s[S::BANK];
+    // the cartridge latches only its own bank bits (F8 one, F6 two); scheme is set before load
+    A = s[S::A]; X = s[S::X]; Y = s[S::Y]; SP = s[S::SP]; P = s[S::P];
+    bank = s[S::BANK] & (scheme == 2 ? 3u : scheme == 1 ? 1u : 0u);
     PC = s[S::PC] | (uint32_t)s[S::PC + 1] << 8;
     uint64_t k = ld64(s + S::CYCLES);
     tim_cw = ld64(s + S::TIM_CW);

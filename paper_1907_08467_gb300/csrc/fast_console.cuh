@@ -101,11 +101,12 @@ __device__ __forceinline__ void fc_cx_eval(IoCtx c, uint32_t upto) {
   if (upto <= from) return;
   c.Sset(IO_CEVAL, upto);
   if (c.T(T_VBLANK) & 2) return;
+  const uint32_t la = from / 228u, xa = from - la * 228u;
+  const uint32_t lb = upto / 228u, xb = upto - lb * 228u;
+  if (la == lb && xb <= 68) return;  // the span lies in one line's horizontal blank
   const uint32_t live = fc_live(c);
   if (__popc(live) < 2) return;
   const uint64_t L0 = c.G64(IO_L0LO), bar = c.G64(IO_BARLO);
-  const uint32_t la = from / 228u, xa = from - la * 228u;
-  const uint32_t lb = upto / 228u, xb = upto - lb * 228u;
   uint32_t x = 0;
   auto seg = [&](uint32_t line, uint32_t x0, uint32_t x1) {
     if (x1 <= 68) return;
@@ -169,6 +170,23 @@ __device__ __noinline__ uint32_t fc_io_read(IoCtx c, uint32_t a, uint32_t t) {
   return (uint32_t)(0xFFull - (n - span)) & 0xFF;
 }
 
+// Append one TIA write record (effect clock, register, value) to the log of
+// a rendered frame.
+__device__ __forceinline__ void fc_log(IoCtx c, uint32_t eff, uint32_t reg, uint32_t v) {
+  const uint32_t lo = c.G(IO_LOGLO), hi = c.G(IO_LOGHI);
+  if (lo | hi) {
+    uint32_t *lp = reinterpret_cast<uint32_t *>((uint64_t)lo | (uint64_t)hi << 32);
+    const uint32_t nrec = c.G(IO_LOGN);
+    if (nrec < c.G(IO_LOGCAP)) lp[nrec] = eff << 14 | reg << 8 | v;
+    else c.Sset(IO_STATUS, c.G(IO_STATUS) | ST_LOG_OVERFLOW);
+    c.Sset(IO_LOGN, nrec + 1);
+  }
+}
+
+// TIA registers whose writes only set a colour or a motion register: logged,
+// no collision or timing effect (COLUP0, COLUP1, COLUPF, COLUBK, HMP0..HMBL).
+constexpr uint64_t FAST_TIA_REGS = (0xFull << 0x06) | (0x1Full << 0x20);
+
 // Write a TIA or RIOT address at cycle t; returns IO_WSYNC / IO_VSYNC_RISE.
 __device__ __noinline__ uint32_t fc_io_write(IoCtx c, uint32_t a, uint32_t v, uint32_t t) {
   if (a & 0x80) {  // RIOT
@@ -186,16 +204,7 @@ __device__ __noinline__ uint32_t fc_io_write(IoCtx c, uint32_t a, uint32_t v, ui
   const uint32_t reg = a & 0x3F;
   const uint32_t eff = 3u * (t + 1u);
   if ((COLL_REGS >> reg) & 1ull) fc_cx_eval(c, eff);
-  if ((LOG_REGS >> reg) & 1ull) {
-    const uint32_t lo = c.G(IO_LOGLO), hi = c.G(IO_LOGHI);
-    if (lo | hi) {
-      uint32_t *lp = reinterpret_cast<uint32_t *>((uint64_t)lo | (uint64_t)hi << 32);
-      const uint32_t nrec = c.G(IO_LOGN);
-      if (nrec < c.G(IO_LOGCAP)) lp[nrec] = eff << 14 | reg << 8 | v;
-      else c.Sset(IO_STATUS, c.G(IO_STATUS) | ST_LOG_OVERFLOW);
-      c.Sset(IO_LOGN, nrec + 1);
-    }
-  }
+  if ((LOG_REGS >> reg) & 1ull) fc_log(c, eff, reg, v);
   uint32_t flags = 0;
   switch (reg) {
     case 0x00:
@@ -275,7 +284,7 @@ struct FastConsole {
   uint32_t pend;           // I/O flags of the current instruction
   uint32_t vs_kf;          // cycle of a VSYNC rise in this frame, ~0 if none
   uint32_t status, instret, frame_no;
-  uint32_t wmask;          // lanes of this warp running envs (cycle-synchronised issue)
+  uint32_t wmask;          // lanes of this warp running envs (lockstep issue)
 
   __device__ __forceinline__ uint32_t P() const {
     return (fn & 0x80) | fv | 0x20 | fdi | ((fz & 0xFF) ? 0u : 2u) | fc;
@@ -289,7 +298,8 @@ struct FastConsole {
     const uint32_t *w = reinterpret_cast<const uint32_t *>(s);
     const uint32_t w0 = w[0], w1 = w[1];
     A = w0 & 0xFF; X = (w0 >> 8) & 0xFF; Y = (w0 >> 16) & 0xFF; SP = w0 >> 24;
-    setP(w1 & 0xFF); bank = (w1 >> 8) & 0xFF; PC = w1 >> 16;
+    setP(w1 & 0xFF); PC = w1 >> 16;
+    bank = (w1 >> 8) & (scheme == 2 ? 3u : scheme == 1 ? 1u : 0u);  // scheme is set before load
     const uint64_t k = (uint64_t)w[2] | (uint64_t)w[3] << 32;
     io.Sset(IO_TCWLO, w[4]); io.Sset(IO_TCWHI, w[5]);
     const uint32_t w6 = w[6], w7 = w[7];
@@ -448,6 +458,27 @@ struct FastConsole {
     if (f & IO_VSYNC_RISE) note_vsync(t);
   }
 
+  // Store instructions write through here (one inlined copy): RAM, cartridge
+  // hotspots, WSYNC and the colour / motion registers inline, every other
+  // TIA or RIOT address through the out-of-line writer.
+  __device__ __forceinline__ void bus_store(uint32_t addr, uint32_t v, uint32_t t) {
+    const uint32_t a = addr & 0x1FFF;
+    if ((a & 0x1280) == 0x0080) { ram[(a & 0x7F) * E] = v & 0xFF; return; }
+    if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
+    if (!(a & 0x80)) {
+      const uint32_t reg = a & 0x3F;
+      if (reg == 0x02) { pend |= IO_WSYNC; return; }
+      if ((FAST_TIA_REGS >> reg) & 1ull) {
+        fc_log(io, 3u * (t + 1u), reg, v & 0xFF);
+        io.Tset(reg < 0x20 ? reg - 2 : reg - 5, v & 0xFF);
+        return;
+      }
+    }
+    const uint32_t f = fc_io_write(io, a, v & 0xFF, t);
+    pend |= f;
+    if (f & IO_VSYNC_RISE) note_vsync(t);
+  }
+
   // ---- ALU ----
   __device__ __forceinline__ void adc(uint32_t v) {
     const uint32_t c = fc;
@@ -504,15 +535,16 @@ struct FastConsole {
   // Returns false (with nothing changed) for the cases the general decoder
   // takes.  Each case sets the cycle count n and the next PC; the tail
   // applies the WSYNC stall.
-  __device__ __forceinline__ bool exec() {
+  // w = the staged word at the current PC (bank * 4096 + (PC & 0xFFF)).
+  __device__ __forceinline__ bool exec(uint32_t w) {
     const uint32_t k0 = kf;
     const uint32_t pc = PC;
     const uint32_t off = pc & 0xFFF;
     if (!(pc & 0x1000) || off > (scheme ? 0xFF3u : 0xFFCu)) return false;
-    const uint32_t w = romw[bank * 4096u + off];
     const uint32_t b1 = (w >> 8) & 0xFF;
     const uint32_t a16 = (w >> 8) & 0xFFFF;
     uint32_t n;
+    uint32_t sa = ~0u, sv = 0, stc = 0;  // pending store: address (~0: none), value, cycle
     pend = 0;
 #define ZPX_ ((b1 + X) & 0xFF)
 #define ZPY_ ((b1 + Y) & 0xFF)
@@ -597,22 +629,22 @@ struct FastConsole {
       case 0x24: { const uint32_t v = rdz(b1, k0 + 2); fn = v; fv = v & 0x40; fz = A & v; n = 3; PC = pc + 2; break; }
       case 0x2C: { const uint32_t v = rd(a16, k0 + 3); fn = v; fv = v & 0x40; fz = A & v; n = 4; PC = pc + 3; break; }
       // stores
-      case 0x85: wrz(b1, A, k0 + 2); n = 3; PC = pc + 2; break;
-      case 0x95: wrz(ZPX_, A, k0 + 3); n = 4; PC = pc + 2; break;
-      case 0x8D: wr(a16, A, k0 + 3); n = 4; PC = pc + 3; break;
-      case 0x9D: wr(ABX_, A, k0 + 4); n = 5; PC = pc + 3; break;
-      case 0x99: wr(ABY_, A, k0 + 4); n = 5; PC = pc + 3; break;
+      case 0x85: sa = b1; sv = A; stc = k0 + 2; n = 3; PC = pc + 2; break;
+      case 0x95: sa = ZPX_; sv = A; stc = k0 + 3; n = 4; PC = pc + 2; break;
+      case 0x8D: sa = a16; sv = A; stc = k0 + 3; n = 4; PC = pc + 3; break;
+      case 0x9D: sa = ABX_; sv = A; stc = k0 + 4; n = 5; PC = pc + 3; break;
+      case 0x99: sa = ABY_; sv = A; stc = k0 + 4; n = 5; PC = pc + 3; break;
       case 0x81: { const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;
-                   wr(ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8, A, k0 + 5); n = 6; PC = pc + 2; break; }
+                   sa = ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8; sv = A; stc = k0 + 5; n = 6; PC = pc + 2; break; }
       case 0x91: { if (!(b1 & 0x80) || b1 == 0xFF) return false;
                    const uint32_t base = ram[(b1 & 0x7F) * E] | ram[((b1 + 1) & 0x7F) * E] << 8;
-                   wr((base + Y) & 0xFFFF, A, k0 + 5); n = 6; PC = pc + 2; break; }
-      case 0x86: wrz(b1, X, k0 + 2); n = 3; PC = pc + 2; break;
-      case 0x96: wrz(ZPY_, X, k0 + 3); n = 4; PC = pc + 2; break;
-      case 0x8E: wr(a16, X, k0 + 3); n = 4; PC = pc + 3; break;
-      case 0x84: wrz(b1, Y, k0 + 2); n = 3; PC = pc + 2; break;
-      case 0x94: wrz(ZPX_, Y, k0 + 3); n = 4; PC = pc + 2; break;
-      case 0x8C: wr(a16, Y, k0 + 3); n = 4; PC = pc + 3; break;
+                   sa = (base + Y) & 0xFFFF; sv = A; stc = k0 + 5; n = 6; PC = pc + 2; break; }
+      case 0x86: sa = b1; sv = X; stc = k0 + 2; n = 3; PC = pc + 2; break;
+      case 0x96: sa = ZPY_; sv = X; stc = k0 + 3; n = 4; PC = pc + 2; break;
+      case 0x8E: sa = a16; sv = X; stc = k0 + 3; n = 4; PC = pc + 3; break;
+      case 0x84: sa = b1; sv = Y; stc = k0 + 2; n = 3; PC = pc + 2; break;
+      case 0x94: sa = ZPX_; sv = Y; stc = k0 + 3; n = 4; PC = pc + 2; break;
+      case 0x8C: sa = a16; sv = Y; stc = k0 + 3; n = 4; PC = pc + 3; break;
       RMW_OPS(0x0A, 0x06, 0x16, 0x0E, 0x1E, asl)
       RMW_OPS(0x4A, 0x46, 0x56, 0x4E, 0x5E, lsr)
       RMW_OPS(0x2A, 0x26, 0x36, 0x2E, 0x3E, rol)
@@ -672,6 +704,7 @@ struct FastConsole {
 #undef RMWM_OPS
 #undef BR
 #undef IMPL
+    if (sa != ~0u) bus_store(sa, sv, stc);
     PC &= 0xFFFF;
     uint32_t k = k0 + n;
     if (pend & IO_WSYNC) k = ((k + 75u) / 76u) * 76u;
@@ -821,25 +854,33 @@ struct FastConsole {
     kf = k;
   }
 
-  // One frame.  Lanes of a warp issue in emulated-cycle order: each round only
-  // the lanes at the warp's smallest cycle count execute an instruction, so
-  // lanes that ran a shorter path wait, and the warp realigns whenever the
-  // programs meet again in time (every WSYNC).  The lane with the smallest
-  // count always advances (every instruction takes at least 2 cycles, and a
-  // frame ends after at most 400 lines), so the loop ends.
+  // One frame.  Lanes of a warp issue in program order of the laggard: each
+  // round the lane with the smallest emulated cycle count leads, and every
+  // lane whose PC equals the leader's executes its instruction with it.  Lanes
+  // that ran a shorter path wait at the join point until the laggard reaches
+  // it, so the warp reconverges on code rather than on time (lanes a few
+  // cycles apart after a page-crossing or a different branch path still run
+  // together), and the executing lanes take one case of the opcode switch.
+  // The leader always advances (every instruction takes at least 2 cycles,
+  // and a frame ends after at most 400 lines), so the loop ends.
   __device__ __forceinline__ uint32_t run_frame() {
     uint32_t next_rel = 0;
     vs_kf = ~0u;
     bool active = true;
     while (__any_sync(wmask, active)) {
+      // next instruction word, fetched before the vote so the two latencies overlap
+      // (bank < banks of the staged cartridge, so the index stays in the stage)
+      const uint32_t w = romw[bank * 4096u + (PC & 0xFFFu)];
       const uint32_t mine = active ? kf : 0xFFFFFFFFu;
       const uint32_t lead = __reduce_min_sync(wmask, mine);
-      if (active && kf == lead) {
+      const uint32_t first = __ffs(__ballot_sync(wmask, active && kf == lead)) - 1;
+      const uint32_t lpc = __shfl_sync(wmask, PC, first);
+      if (active && PC == lpc) {
         if (jam) {
           next_rel = kf / 76u;
           active = false;
         } else {
-          if (!exec()) fc_exec_general(this);
+          if (!exec(w)) fc_exec_general(this);
           if (jam) { next_rel = kf / 76u; active = false; }
           else if (vs_kf != ~0u) { next_rel = vs_kf / 76u; active = false; }
           else if (kf >= 76u * CAP_LINES) { status |= ST_FRAME_CAP; next_rel = kf / 76u; active = false; }

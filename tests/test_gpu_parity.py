@@ -250,3 +250,27 @@ def test_batched_equals_plain_at_full_size():
         ob, rb, db = b.step(x)
         assert torch.equal(oa, ob) and torch.equal(ra, rb) and torch.equal(da, db), s
     assert torch.equal(a.state(), b.state())
+
+
+@pytest.mark.parametrize("form", ["plain", "batched-auto"])
+def test_state_with_extra_bank_bits_matches_oracle(form):
+    """States whose bank byte has bits the cartridge does not latch (4 KB, F8
+    and F6 envs) load as the cartridge's bits on both sides and step alike."""
+    w = synth.workload(3, n_envs=32)
+    env_rom = [0] * 4 + [12] * 4 + [22] * 4
+    g, o = pair(w.roms, env_rom, sticky=True, seed=3, **FORMS[form])
+    acts = synth.actions(23, 4, len(env_rom))
+    run_parity(g, o, acts[:1])
+    st = o.state()
+    st[:, 0x05] |= np.array([0xFC, 0xFE, 0x80, 0x40] * 3, np.uint8)
+    g.set_state(torch.from_numpy(st).cuda())
+    o.set_state(st)
+    assert_same("masked bank", o.state()[:, 0x05], st[:, 0x05] & np.array([0] * 4 + [1] * 4 + [3] * 4, np.uint8))
+    # the device keeps the bytes as given until a step loads them
+    obs, rew, done = g.step(torch.from_numpy(acts[1]).cuda())
+    oo, orw, od = o.step(acts[1])
+    torch.cuda.synchronize()
+    assert_same("rewards", rew.cpu().numpy(), orw)
+    assert_same("dones", done.cpu().numpy(), od)
+    assert_same("obs", obs.cpu().numpy(), oo)
+    run_parity(g, o, acts[2:])

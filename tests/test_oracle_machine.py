@@ -510,3 +510,15 @@ Start:  LDA #$F0
     m.set_action(3)   # RIGHT: input pins 0x7F; output bits 7..4 come from the latch
     run_to_jam(m)
     assert m.ram()[0] == 0x5F
+
+
+def test_state_bank_byte_keeps_only_the_cartridges_bank_bits():
+    """A 2K/4K cartridge has no bank latch, F8 one bank bit and F6 two: a
+    state whose bank byte has more bits set loads as those bits only."""
+    for size, mask in [(2048, 0), (4096, 0), (8192, 1), (16384, 3)]:
+        m = OracleMachine(bytes(size))
+        for b in (0xFF, 0xFE, 0x05, 0x02):
+            s = m.state()
+            s[0x05] = b
+            m.set_state(s)
+            assert m.state()[0x05] == b & mask, (size, b)
