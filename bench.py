@@ -31,15 +31,25 @@ sys.path.insert(0, ROOT)
 METRIC = "raw emulated frames/sec on 1 GB300 vs plain GPU path and CPU oracle; p50/p99 step ms"
 SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 
-# Warp instructions issued per env-frame by the interpreter kernel on the
-# default workload (sprite, 4096 envs) and DRAM bytes per env-step, from the
-# ncu capture summarised in profiles/interpreter_batched_sprite4096.md
-# (smsp__inst_executed.sum and dram__bytes_read.sum + dram__bytes_write.sum
-# of one launch, divided by its 16384 env-frames / 4096 env-steps), keyed by
-# (form, envs per warp).  Refresh whenever the interpreter changes; a shape
+# Warp instructions issued per env-frame by the interpreter kernel and DRAM
+# bytes per env-step, from the ncu captures summarised in
+# profiles/interpreter_batched_sprite4096.md (smsp__inst_executed.sum and
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, divided by its
+# 16384 env-frames / 4096 env-steps), keyed by (workload config, form, envs
+# per warp).  They hold for the interpreter version captured there; a key
 # without an entry reports achieved = null.
-INTERP_WARP_INST_PER_ENV_FRAME = {("batched", 4): 5278237589 / 16384}
-INTERP_DRAM_BYTES_PER_ENV_STEP = {("batched", 4): (4978432 + 475136) / 4096}
+INTERP_WARP_INST_PER_ENV_FRAME = {(2, "batched", 16): 1045274177 / 16384, (2, "batched", 32): 527823221 / 16384}
+INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 16): (1378304 + 68608) / 4096,
+                                  (2, "batched", 32): (1380608 + 67328) / 4096}
+# Algorithmic bytes of the fused rasterise + preprocess kernel per env-step,
+# besides 4 bytes per logged TIA write: snapshots and record counts of the two
+# rendered frames (2 x 64 + 2 x 8), the three older stack planes read from the
+# ring, the 84x84x4 stack written out, the new plane written to the ring and
+# the ring head.
+FUSED_FIXED_BYTES_PER_ENV_STEP = 2 * 64 + 2 * 8 + 3 * 7056 + 4 * 7056 + 7056 + 1
+# DRAM bytes per env-step of the fused kernel from the capture summarised in
+# profiles/raster_preprocess_fused_sprite4096.md.
+FUSED_DRAM_BYTES_PER_ENV_STEP = {2: (107876608 + 94087168) / 4096}
 
 
 def parse():
@@ -404,7 +414,7 @@ def main():
     roof = None
     if interp_n:
         dur = interp_ms / interp_n / 1000.0
-        shape_key = (args.form, env.launch_shape()[0])
+        shape_key = (args.config, args.form, env.launch_shape()[0])
         per = INTERP_WARP_INST_PER_ENV_FRAME.get(shape_key)
         peak = SM_COUNT * SMSP_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
         ach = per * w.n_envs * w.frameskip / dur / 1e9 if per else None
@@ -415,6 +425,20 @@ def main():
                 "share_of_step": interp_ms / max(1e-9, sum(v[0] for v in prof.values())),
                 "m6502_inst_per_s": instr / total_s / 1e6 if instr else None,
                 "peak_source": "152 SMs x 4 schedulers x 2070 MHz (issue slots)"}
+    # the fused rasterise + preprocess kernel against HBM (its design bound)
+    roof2 = None
+    fused_ms, fused_n = prof.get("fused_raster_preprocess", (0.0, 0))
+    if fused_n and not inference:
+        dur = fused_ms / fused_n / 1000.0
+        per_step = FUSED_FIXED_BYTES_PER_ENV_STEP + 4.0 * (logrec / K if K else 0.0) / w.n_envs
+        hbm = load_peaks().get("hbm_gbs")
+        ach = per_step * w.n_envs / dur / 1e9
+        tb = FUSED_DRAM_BYTES_PER_ENV_STEP.get(args.config)
+        roof2 = {"bound": "hbm", "kernel": "fused_raster_preprocess", "achieved": ach,
+                 "peak": hbm if hbm else 6800.0, "unit": "GB/s", "frac": ach / (hbm if hbm else 6800.0),
+                 "traffic": tb * w.n_envs if tb else None, "algorithmic_bytes_per_env_step": per_step,
+                 "launch_ms": dur * 1000.0,
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if hbm else "fallback 6.8 TB/s"}
     kernels = {k: {"ms_per_launch": v[0] / max(1, v[1]), "launches": v[1]} for k, v in prof.items()}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -432,7 +456,7 @@ def main():
                        "launch_shape": dict(zip(["envs_per_warp", "envs_per_block", "warps_per_frame", "grid"],
                                                 env.launch_shape())),
                        "parallelism": f"replicas x{ws}"},
-            "e2e": e2e, "roofline": roof, "kernels": kernels, "gpu_launches": gpu_launches,
+            "e2e": e2e, "roofline": roof, "roofline_fused": roof2, "kernels": kernels, "gpu_launches": gpu_launches,
             "m6502_inst_per_step": instr / K if K else None, "tia_log_records_per_step": logrec / K if K else None,
             "wall_s": wall, "clocks": clk, "cpu_baseline": cpu,
         }

@@ -40,51 +40,68 @@ __device__ __forceinline__ float exp_cw(float x) {
   return __fmul_rn(p, __int_as_float((k + 127) << 23));
 }
 
-// One block of 512 threads per env: thread c accumulates chunk c (c < 441).
-__global__ void __launch_bounds__(512) k_policy(const uint8_t *obs, const uint16_t *W, const uint8_t *state,
-                                                uint8_t *actions, float *logits_out, int n, uint64_t seed) {
-  __shared__ float part[POLICY_A][512];
-  const int i = blockIdx.x, t = threadIdx.x;
-  if (i >= n) return;
-  float acc[POLICY_A];
-#pragma unroll
-  for (int j = 0; j < POLICY_A; ++j) acc[j] = 0.0f;
-  if (t < POLICY_CHUNKS) {
-    const uint4 *x4 = reinterpret_cast<const uint4 *>(obs + (size_t)i * POLICY_K + (size_t)t * 64);
-    const uint32_t *w32 = reinterpret_cast<const uint32_t *>(W + (size_t)t * 64 * POLICY_A);
+constexpr int POLICY_TPB = 64;     // envs (threads) per block
+constexpr int POLICY_DEPTH = 9;    // partial-sum stack entries: the tree over 512 slots has 9 levels
+
+// One thread per env.  The tree's leaves (the 512 chunk slots, 441 chunks
+// and zero padding) are visited in bit-reversed slot order k -> c = rev9(k).
+// In that order the two slots the tree adds at every level (i and i + h)
+// are neighbours, so the tree is the one a binary counter builds from left
+// to right.  Each chunk partial is pushed on a stack and added to the entries
+// below it as the carry of k ripples (leaf k merges trailing_ones(k) times):
+// the same additions of the same operands as the halving tree, hence the same
+// bits.  The block stages chunk c of W, widened to fp32 (exact), in shared
+// memory once for all its envs; every env's 84x84x4 stack is read once.
+__global__ void __launch_bounds__(POLICY_TPB) k_policy(const uint8_t *obs, const uint16_t *W, const uint8_t *state,
+                                                      uint8_t *actions, float *logits_out, int n, uint64_t seed) {
+  __shared__ float wsm[64 * POLICY_A];
+  __shared__ float stk[POLICY_DEPTH * POLICY_A][POLICY_TPB];
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * POLICY_TPB + t;
+  const bool live = i < n;
+  const uint8_t *xs = obs + (size_t)(live ? i : 0) * POLICY_K;  // idle threads read env 0 and discard it
+  int sp = 0;
 #pragma unroll 1
-    for (int q4 = 0; q4 < 4; ++q4) {
-      const uint4 xv4 = x4[q4];
-      const uint32_t xw[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
+  for (uint32_t k = 0; k < 512; ++k) {
+    const uint32_t c = __brev(k) >> 23;
+    float acc[POLICY_A];
 #pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        const float xv = (float)((xw[b >> 2] >> (8 * (b & 3))) & 0xFF);
-        const uint32_t *wr = w32 + (q4 * 16 + b) * (POLICY_A / 2);
+    for (int j = 0; j < POLICY_A; ++j) acc[j] = 0.0f;
+    if (c < (uint32_t)POLICY_CHUNKS) {  // the same for every thread of the block
+      __syncthreads();                  // the previous chunk's readers are done
+      const uint16_t *wc = W + (size_t)c * 64 * POLICY_A;
+      for (int q = t; q < 64 * POLICY_A; q += POLICY_TPB) wsm[q] = __uint_as_float((uint32_t)wc[q] << 16);
+      __syncthreads();
+      const uint4 *x4 = reinterpret_cast<const uint4 *>(xs + (size_t)c * 64);
+#pragma unroll 1
+      for (int q4 = 0; q4 < 4; ++q4) {
+        const uint4 xv4 = x4[q4];
+        const uint32_t xw[4] = {xv4.x, xv4.y, xv4.z, xv4.w};
 #pragma unroll
-        for (int j2 = 0; j2 < POLICY_A / 2; ++j2) {
-          const uint32_t pair = __ldg(wr + j2);
-          acc[2 * j2] = __fmaf_rn(xv, __uint_as_float(pair << 16), acc[2 * j2]);
-          acc[2 * j2 + 1] = __fmaf_rn(xv, __uint_as_float(pair & 0xFFFF0000u), acc[2 * j2 + 1]);
+        for (int b = 0; b < 16; ++b) {
+          const float xv = (float)((xw[b >> 2] >> (8 * (b & 3))) & 0xFF);
+          const float *wr = wsm + (q4 * 16 + b) * POLICY_A;
+#pragma unroll
+          for (int j = 0; j < POLICY_A; ++j) acc[j] = __fmaf_rn(xv, wr[j], acc[j]);
         }
       }
     }
-  }
+#pragma unroll 1
+    for (uint32_t m = __ffs(~k) - 1; m > 0; --m) {
+      --sp;
 #pragma unroll
-  for (int j = 0; j < POLICY_A; ++j) part[j][t] = acc[j];
-  __syncthreads();
-  for (int h = 256; h >= 1; h >>= 1) {
-    if (t < h) {
-#pragma unroll
-      for (int j = 0; j < POLICY_A; ++j) part[j][t] = __fadd_rn(part[j][t], part[j][t + h]);
+      for (int j = 0; j < POLICY_A; ++j) acc[j] = __fadd_rn(stk[sp * POLICY_A + j][t], acc[j]);
     }
-    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < POLICY_A; ++j) stk[sp * POLICY_A + j][t] = acc[j];
+    ++sp;
   }
-  if (t == 0) {
+  if (live) {
     float l[POLICY_A];
-    float m = part[0][0];
+    float m = stk[0][t];
 #pragma unroll
     for (int j = 0; j < POLICY_A; ++j) {
-      l[j] = part[j][0];
+      l[j] = stk[j][t];
       m = l[j] > m ? l[j] : m;
     }
     float e[POLICY_A], tot = 0.0f;
