@@ -213,14 +213,16 @@ __device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uin
       const uint32_t rec = __shfl_sync(0xFFFFFFFFu, chunk, ri - base);
       const uint32_t c = rec >> 14;
       if (c >= end) break;
+      R.prepare(k < 5 && cl + 68u + lane + 32u * k < c, lane);
       while (k < 5 && cl + 68u + lane + 32u * k < c) {
-        row[lane + 32 * k] = (uint8_t)R.pixel(lane + 32 * k, line);
+        row[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
         ++k;
       }
       R.apply((rec >> 8) & 0x3F, rec & 0xFF, c);
       ++ri;
     }
-    for (; k < 5; ++k) row[lane + 32 * k] = (uint8_t)R.pixel(lane + 32 * k, line);
+    R.prepare(k < 5, lane);
+    for (; k < 5; ++k) row[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
   }
 }
 

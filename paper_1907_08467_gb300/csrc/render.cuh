@@ -18,6 +18,11 @@ struct RenderRegs {
   uint32_t vdelp0, vdelp1, vdelbl, resmp0, resmp1, hmp0, hmp1, hmm0, hmm1, hmbl;
   uint32_t p0, p1, m0, m1, bl;
   uint32_t bar;  // frame-relative line of the HMOVE bar, or ~0u
+  // Per lane: bit k of v_* = the object covers column lane + 32k (players,
+  // missiles and ball with their enables, playfield).  Rebuilt from the
+  // objects' 160-bit masks for the objects in `dirty` before the next pixel.
+  uint32_t vp0, vp1, vm0, vm1, vbl, vpf;
+  uint32_t dirty;  // 1 P0, 2 P1, 4 M0, 8 M1, 16 BL, 32 PF
 
   // from a 64-byte snapshot (canonical bytes 0x20..0x5F)
   __device__ void load(const uint8_t *t) {
@@ -30,6 +35,7 @@ struct RenderRegs {
     uint64_t b = 0, l0 = 0;
     for (int i = 7; i >= 0; --i) { b = (b << 8) | t[40 + i]; l0 = (l0 << 8) | t[48 + i]; }
     bar = (b != NO_LINE && b >= l0 && b - l0 < 1024) ? (uint32_t)(b - l0) : ~0u;
+    dirty = 63;
   }
 
   static __device__ __forceinline__ uint32_t res_pos(uint32_t eff, uint32_t add, uint32_t hb) {
@@ -50,87 +56,85 @@ struct RenderRegs {
   __device__ void apply(uint32_t reg, uint32_t v, uint32_t eff) {
     switch (reg) {
       case 0x01: vblank = v; break;
-      case 0x04: nusiz0 = v; break;
-      case 0x05: nusiz1 = v; break;
+      case 0x04: nusiz0 = v; dirty |= 1 | 4; break;
+      case 0x05: nusiz1 = v; dirty |= 2 | 8; break;
       case 0x06: colup0 = v; break;
       case 0x07: colup1 = v; break;
       case 0x08: colupf = v; break;
       case 0x09: colubk = v; break;
-      case 0x0A: ctrlpf = v; break;
-      case 0x0B: refp0 = v; break;
-      case 0x0C: refp1 = v; break;
-      case 0x0D: pf0 = v; break;
-      case 0x0E: pf1 = v; break;
-      case 0x0F: pf2 = v; break;
-      case 0x10: p0 = res_pos(eff, 5, 3); break;
-      case 0x11: p1 = res_pos(eff, 5, 3); break;
-      case 0x12: m0 = res_pos(eff, 4, 2); break;
-      case 0x13: m1 = res_pos(eff, 4, 2); break;
-      case 0x14: bl = res_pos(eff, 4, 2); break;
-      case 0x1B: grp0_new = v; grp1_old = grp1_new; break;
-      case 0x1C: grp1_new = v; grp0_old = grp0_new; enabl_old = enabl_new; break;
-      case 0x1D: enam0 = v; break;
-      case 0x1E: enam1 = v; break;
-      case 0x1F: enabl_new = v; break;
+      case 0x0A: ctrlpf = v; dirty |= 16 | 32; break;
+      case 0x0B: refp0 = v; dirty |= 1; break;
+      case 0x0C: refp1 = v; dirty |= 2; break;
+      case 0x0D: pf0 = v; dirty |= 32; break;
+      case 0x0E: pf1 = v; dirty |= 32; break;
+      case 0x0F: pf2 = v; dirty |= 32; break;
+      case 0x10: p0 = res_pos(eff, 5, 3); dirty |= 1; break;
+      case 0x11: p1 = res_pos(eff, 5, 3); dirty |= 2; break;
+      case 0x12: m0 = res_pos(eff, 4, 2); dirty |= 4; break;
+      case 0x13: m1 = res_pos(eff, 4, 2); dirty |= 8; break;
+      case 0x14: bl = res_pos(eff, 4, 2); dirty |= 16; break;
+      case 0x1B: grp0_new = v; grp1_old = grp1_new; dirty |= 1 | 2; break;
+      case 0x1C: grp1_new = v; grp0_old = grp0_new; enabl_old = enabl_new; dirty |= 1 | 2 | 16; break;
+      case 0x1D: enam0 = v; dirty |= 4; break;
+      case 0x1E: enam1 = v; dirty |= 8; break;
+      case 0x1F: enabl_new = v; dirty |= 16; break;
       case 0x20: hmp0 = v; break;
       case 0x21: hmp1 = v; break;
       case 0x22: hmm0 = v; break;
       case 0x23: hmm1 = v; break;
       case 0x24: hmbl = v; break;
-      case 0x25: vdelp0 = v; break;
-      case 0x26: vdelp1 = v; break;
-      case 0x27: vdelbl = v; break;
+      case 0x25: vdelp0 = v; dirty |= 1; break;
+      case 0x26: vdelp1 = v; dirty |= 2; break;
+      case 0x27: vdelbl = v; dirty |= 16; break;
       case 0x28:
         if ((resmp0 & 2) && !(v & 2)) m0 = (p0 + ((nusiz0 & 7) == 5 ? 8u : (nusiz0 & 7) == 7 ? 16u : 4u)) % 160u;
-        resmp0 = v; break;
+        resmp0 = v; dirty |= 4; break;
       case 0x29:
         if ((resmp1 & 2) && !(v & 2)) m1 = (p1 + ((nusiz1 & 7) == 5 ? 8u : (nusiz1 & 7) == 7 ? 16u : 4u)) % 160u;
-        resmp1 = v; break;
+        resmp1 = v; dirty |= 8; break;
       case 0x2A:
         p0 = move(p0, hmp0); p1 = move(p1, hmp1); m0 = move(m0, hmm0); m1 = move(m1, hmm1); bl = move(bl, hmbl);
         if (eff % 228u < 68u) bar = eff / 228u;
+        dirty |= 1 | 2 | 4 | 8 | 16;
         break;
       case 0x2B: hmp0 = hmp1 = hmm0 = hmm1 = hmbl = 0; break;
       default: break;
     }
   }
 
-  // copy slots 0,1,2 (offsets 0,16,32) and slot 4 (offset 64) of a NUSIZ value
-  static __device__ __forceinline__ uint32_t slots(uint32_t nusiz) {
-    uint32_t c = copy_bits(nusiz);
-    return (c & 7) | ((c & 8) << 1);
+  static __device__ __forceinline__ uint32_t lane_bits(const M160 &m, uint32_t lane) {
+    return ((m.w0 >> lane) & 1u) | ((m.w1 >> lane) & 1u) << 1 | ((m.w2 >> lane) & 1u) << 2 |
+           ((m.w3 >> lane) & 1u) << 3 | ((m.w4 >> lane) & 1u) << 4;
   }
-  static __device__ __forceinline__ uint32_t dist(uint32_t col, uint32_t pos) {
-    return col >= pos ? col - pos : col + 160 - pos;
+  __device__ __forceinline__ void refresh(uint32_t lane) {
+    if (dirty & 1) {
+      const uint32_t g = (vdelp0 & 1) ? grp0_old : grp0_new;
+      vp0 = g ? lane_bits(player_mask(g, refp0, nusiz0, p0), lane) : 0u;
+    }
+    if (dirty & 2) {
+      const uint32_t g = (vdelp1 & 1) ? grp1_old : grp1_new;
+      vp1 = g ? lane_bits(player_mask(g, refp1, nusiz1, p1), lane) : 0u;
+    }
+    if (dirty & 4) vm0 = ((enam0 & 2) && !(resmp0 & 2)) ? lane_bits(missile_mask(nusiz0, m0), lane) : 0u;
+    if (dirty & 8) vm1 = ((enam1 & 2) && !(resmp1 & 2)) ? lane_bits(missile_mask(nusiz1, m1), lane) : 0u;
+    if (dirty & 16) vbl = ((((vdelbl & 1) ? enabl_old : enabl_new) & 2)) ? lane_bits(ball_mask(ctrlpf, bl), lane) : 0u;
+    if (dirty & 32) vpf = lane_bits(pf_mask(pf0, pf1, pf2, ctrlpf), lane);
+    dirty = 0;
   }
-  static __device__ __forceinline__ bool player_on(uint32_t g, uint32_t refp, uint32_t nusiz, uint32_t pos, uint32_t col) {
-    if (!g) return false;
-    uint32_t mode = nusiz & 7;
-    uint32_t sh = mode == 5 ? 1u : mode == 7 ? 2u : 0u;
-    uint32_t sl = (mode == 5 || mode == 7) ? 1u : slots(nusiz);
-    uint32_t idx = dist(col, pos) >> sh;
-    if (idx >= 80 || !((sl >> (idx >> 4)) & 1u) || (idx & 8)) return false;
-    return (player_bits(g, refp) >> (idx & 7)) & 1u;
+  // Rebuild the stale coverage bits if any lane of the warp is about to draw
+  // (draws = this lane has a pixel to draw before the next register write).
+  // Every lane applies the same writes, so `dirty` is the same in all lanes
+  // and the rebuild runs once for the whole warp.
+  __device__ __forceinline__ void prepare(bool draws, uint32_t lane) {
+    if (__any_sync(0xFFFFFFFFu, draws && dirty != 0)) refresh(lane);
   }
-  static __device__ __forceinline__ bool missile_on(uint32_t enam, uint32_t resmp, uint32_t nusiz, uint32_t pos, uint32_t col) {
-    if (!(enam & 2) || (resmp & 2)) return false;
-    uint32_t mode = nusiz & 7;
-    uint32_t sl = (mode == 5 || mode == 7) ? 1u : slots(nusiz);
-    uint32_t d = dist(col, pos);
-    if (d >= 80 || !((sl >> (d >> 4)) & 1u)) return false;
-    return (d & 15) < (1u << ((nusiz >> 4) & 3));
-  }
-  __device__ __forceinline__ uint32_t pixel(uint32_t col, uint32_t line) const {
-    if ((vblank & 2) || (line == bar && col < 8)) return 0;
-    bool P0 = player_on((vdelp0 & 1) ? grp0_old : grp0_new, refp0, nusiz0, p0, col);
-    bool P1 = player_on((vdelp1 & 1) ? grp1_old : grp1_new, refp1, nusiz1, p1, col);
-    bool M0 = missile_on(enam0, resmp0, nusiz0, m0, col);
-    bool M1 = missile_on(enam1, resmp1, nusiz1, m1, col);
-    bool BL = (((vdelbl & 1) ? enabl_old : enabl_new) & 2) && dist(col, bl) < (1u << ((ctrlpf >> 4) & 3));
-    uint32_t half = col >= 80 ? 1u : 0u;
-    uint32_t b = (col - 80u * half) >> 2;
-    if (half && (ctrlpf & 1)) b = 19 - b;
-    bool PF = (pf20(pf0, pf1, pf2) >> b) & 1u;
+  // Pixel of column lane + 32k on a frame-relative line (the lane's own column);
+  // prepare() has run since the last write.
+  __device__ __forceinline__ uint32_t pixel_k(uint32_t k, uint32_t lane, uint32_t line) const {
+    if ((vblank & 2) || (k == 0 && line == bar && lane < 8)) return 0;
+    const bool P0 = (vp0 >> k) & 1u, P1 = (vp1 >> k) & 1u, M0 = (vm0 >> k) & 1u, M1 = (vm1 >> k) & 1u;
+    const bool BL = (vbl >> k) & 1u, PF = (vpf >> k) & 1u;
+    const bool half = lane + 32u * k >= 80u;
     uint32_t c;
     if (ctrlpf & 4) {
       c = (PF || BL) ? colupf : (P0 || M0) ? colup0 : (P1 || M1) ? colup1 : colubk;
@@ -141,6 +145,7 @@ struct RenderRegs {
     }
     return c & 0xFE;
   }
+
 };
 
 // Render one frame with one warp.  recs: log records; row_buf: 160 bytes of
@@ -166,14 +171,16 @@ __device__ inline void render_frame_warp(RenderRegs &R, const uint32_t *recs, ui
         const uint32_t rec = __shfl_sync(0xFFFFFFFFu, chunk, ri - base);
         const uint32_t c = rec >> 14;
         if (c >= end) break;
+        R.prepare(k < 5 && cl + 68u + lane + 32u * k < c, lane);
         while (k < 5 && cl + 68u + lane + 32u * k < c) {
-          row_buf[lane + 32 * k] = (uint8_t)R.pixel(lane + 32 * k, line);
+          row_buf[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
           ++k;
         }
         R.apply((rec >> 8) & 0x3F, rec & 0xFF, c);
         ++ri;
       }
-      for (; k < 5; ++k) row_buf[lane + 32 * k] = (uint8_t)R.pixel(lane + 32 * k, line);
+      R.prepare(k < 5, lane);
+      for (; k < 5; ++k) row_buf[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
     }
     __syncwarp();
     const uint32_t *src = reinterpret_cast<const uint32_t *>(row_buf);
