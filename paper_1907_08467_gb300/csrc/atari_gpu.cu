@@ -462,11 +462,11 @@ struct atari_env {
   uint8_t *d_act = nullptr;   // staging for atari_env_step_host
   uint8_t *d_obs_tmp = nullptr;
   // batched form
-  uint32_t *d_romw = nullptr;       // [n_roms][16384] staged-ROM words
+  uint8_t *d_romb = nullptr;        // [n_roms][16384] cartridge bytes for the batched stage
   uint8_t *d_dec_op = nullptr;      // 512 bytes
   int32_t *d_grp = nullptr;         // rom, start, count per work item (3 * n_groups) then perm (n)
   int *d_queue = nullptr;
-  int n_groups = 0, lanes = 32, warps = 4, wpf = 4, grid = 0, romw_words = 4096, max_blocks = 1;
+  int n_groups = 0, lanes = 32, warps = 4, wpf = 4, grid = 0, rom_stage = 4096, max_blocks = 1;
   std::vector<int32_t> h_env_rom;
   std::vector<uint32_t> h_banks;
   cudaStream_t cap_stream = nullptr;
@@ -541,7 +541,7 @@ int build_groups(atari_env *E, int lanes, int warps) {
   E->n_groups = ng;
   E->lanes = lanes;
   E->warps = warps;
-  size_t smem = (size_t)E->romw_words * 4 + 512 + (size_t)lanes * warps * (512 + 4 * IO_WORDS + TIA_BYTES);
+  size_t smem = (size_t)E->rom_stage + 16 + 512 + (size_t)lanes * warps * (512 + 4 * IO_WORDS + TIA_BYTES);
   int per_sm = 0;
   CUDA_TRY(cudaFuncSetAttribute(k_interp_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched, warps * 32, smem));
@@ -559,7 +559,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
   BatchArgs a;
   a.state = E->d_state;
   a.cache = E->d_cache;
-  a.romw = E->d_romw;
+  a.romb = E->d_romb;
   a.info = E->d_info;
   a.dec_op = E->d_dec_op;
   a.actions = d_actions;
@@ -580,7 +580,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
   a.n_groups = E->n_groups;
   a.lanes = E->lanes;
   a.E = E->lanes * E->warps;
-  a.romw_words = E->romw_words;
+  a.rom_stage = E->rom_stage;
   a.frameskip = c.frameskip;
   a.sticky = c.sticky;
   a.n_cache = c.n_cache;
@@ -591,7 +591,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
 }
 
 size_t interp_smem(const atari_env *E) {
-  return (size_t)E->romw_words * 4 + 512 + (size_t)E->lanes * E->warps * (512 + 4 * IO_WORDS + TIA_BYTES);
+  return (size_t)E->rom_stage + 16 + 512 + (size_t)E->lanes * E->warps * (512 + 4 * IO_WORDS + TIA_BYTES);
 }
 size_t fused_smem() { return 2 * 210 * 160 + 128 + 7056; }
 
@@ -663,7 +663,7 @@ size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg) {
   b += n * 2 * (size_t)cfg->log_cap * 4;                  // log
   b += n * 2 * 64 + n * 2 * 2 * 4;                        // snapshots, meta
   if (cfg->form == ATARI_FORM_PLAIN) b += n * 2 * 210 * 160;   // frames (plain form only)
-  else b += (size_t)n_roms * 16384 * 4 + 512 + n * 4 + 64;     // staged-ROM words, work items
+  else b += (size_t)n_roms * 16384 + 512 + n * 4 + 64;         // cartridge bytes for the stage, work items
   if (cfg->output_mode == ATARI_OUT_STACK) b += n * 4 * 7056 + n;
   b += n * (4 + 1 + 8 + 1);                               // rewards, dones, counters, action staging
   return b;
@@ -794,7 +794,7 @@ void atari_env_destroy(atari_env *E) {
   if (!E) return;
   void *ptrs[] = {E->d_roms, E->d_info, E->d_dec, E->d_env_rom, E->d_env_key, E->d_state, E->d_cache, E->d_log,
                   E->d_snap, E->d_meta, E->d_frames, E->d_ring, E->d_head, E->d_luma, E->d_rew, E->d_done,
-                  E->d_ctr, E->d_act, E->d_obs_tmp, E->d_romw, E->d_dec_op, E->d_grp, E->d_queue};
+                  E->d_ctr, E->d_act, E->d_obs_tmp, E->d_romb, E->d_dec_op, E->d_grp, E->d_queue};
   for (auto &g : E->graphs) cudaGraphExecDestroy(g.exec);
   if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
   for (void *p : ptrs)
@@ -1014,7 +1014,7 @@ int autotune(atari_env *E) {
 
 int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vector<uint32_t> &dec) {
   const int R = E->n_roms;
-  std::vector<uint32_t> words((size_t)R * 16384, 0u);
+  std::vector<uint8_t> bytes((size_t)R * 16384, 0u);
   std::vector<uint8_t> dec_op(512, 0);
   auto info_of = [&](uint32_t opc) {
     uint32_t t = dec[opc];
@@ -1028,20 +1028,14 @@ int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vect
   for (int r = 0; r < R; ++r) {
     const uint32_t banks = E->h_banks[r];
     max_banks = std::max(max_banks, banks);
-    for (uint32_t b = 0; b < banks; ++b) {
-      const uint8_t *bk = img.data() + (size_t)r * ROM_SLOT + b * 4096;
-      for (uint32_t o = 0; o < 4096; ++o) {
-        uint32_t b0 = bk[o], b1 = o + 1 < 4096 ? bk[o + 1] : 0u, b2 = o + 2 < 4096 ? bk[o + 2] : 0u;
-        words[(size_t)r * 16384 + b * 4096 + o] = b0 | b1 << 8 | b2 << 16 | info_of(b0) << 24;
-      }
-    }
+    memcpy(bytes.data() + (size_t)r * 16384, img.data() + (size_t)r * ROM_SLOT, (size_t)banks * 4096);
   }
-  E->romw_words = (int)max_banks * 4096;
+  E->rom_stage = (int)max_banks * 4096;
   size_t &T = E->bytes;
-  if (int rc = dalloc(&E->d_romw, words.size() * 4, T)) return rc;
+  if (int rc = dalloc(&E->d_romb, bytes.size(), T)) return rc;
   if (int rc = dalloc(&E->d_dec_op, 512, T)) return rc;
   if (int rc = dalloc(&E->d_queue, 64, T)) return rc;
-  CUDA_TRY(cudaMemcpy(E->d_romw, words.data(), words.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(E->d_romb, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(E->d_dec_op, dec_op.data(), 512, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
   CUDA_TRY(cudaFuncSetAttribute(k_raster_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem()));

@@ -25,7 +25,7 @@ namespace atari {
 struct BatchArgs {
   uint8_t *state;
   const uint8_t *cache;
-  const uint32_t *romw;      // [n_roms][16384] staged-ROM words
+  const uint8_t *romb;       // [n_roms][16384] cartridge bytes, banks of 4096
   const uint32_t *info;      // per ROM: scheme | score << 8 | gameover << 16 | banks << 24
   const uint8_t *dec_op;     // 512 bytes: op per opcode, then mode/cycles/penalty per opcode
   const uint8_t *actions;
@@ -40,7 +40,7 @@ struct BatchArgs {
   const int32_t *grp_rom, *grp_start, *grp_count, *perm;
   const int32_t *opos;       // null, or the packed action/output position of each work-list entry
   int *queue;
-  int n_groups, lanes, E, romw_words;
+  int n_groups, lanes, E, rom_stage;  // rom_stage: bytes staged per block (largest cartridge)
   int frameskip, sticky, n_cache, log_cap, first_slot;
   uint64_t seed;
 };
@@ -126,8 +126,8 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
 
 __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t *romw = reinterpret_cast<uint32_t *>(smem);
-  uint8_t *dec_op = smem + (size_t)a.romw_words * 4;
+  uint8_t *rom8 = smem;                                  // rom_stage bytes, then 16 of padding
+  uint8_t *dec_op = smem + (size_t)a.rom_stage + 16;
   uint32_t *ram = reinterpret_cast<uint32_t *>(dec_op + 512);
   uint32_t *iow = ram + 128 * a.E;
   uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_WORDS * a.E);
@@ -144,9 +144,10 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
     const int rom = a.grp_rom[g];
     if (rom != cur_rom) {
       const uint32_t banks = a.info[rom] >> 24;
-      const uint4 *src = reinterpret_cast<const uint4 *>(a.romw + (size_t)rom * 16384);
-      uint4 *dst = reinterpret_cast<uint4 *>(romw);
-      for (uint32_t q = threadIdx.x; q < banks * 1024u; q += blockDim.x) dst[q] = src[q];
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.romb + (size_t)rom * 16384);
+      uint4 *dst = reinterpret_cast<uint4 *>(rom8);
+      for (uint32_t q = threadIdx.x; q < banks * 256u; q += blockDim.x) dst[q] = src[q];
+      if (threadIdx.x == 0) dst[banks * 256u] = make_uint4(0, 0, 0, 0);
       cur_rom = rom;
       __syncthreads();
     }
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
         uint8_t *st = a.state + (size_t)i * 256;
         const uint32_t inf = a.info[rom];
         FastConsole m;
-        m.romw = romw;
+        m.rom8 = rom8;
         m.dec_op = dec_op;
         m.ram = ram + j;
         m.io = IoCtx{tia + j, iow + j, (uint32_t)a.E};

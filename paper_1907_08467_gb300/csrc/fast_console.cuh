@@ -12,8 +12,9 @@
 //     latches, RIOT timer and ports, inputs, log cursor, frame base line)
 //     in shared memory, interleaved the same way, touched only by the
 //     out-of-line I/O functions below;
-//   - the block's cartridge staged in shared memory as one word per byte
-//     offset (bytes off .. off+3), so an instruction is fetched with one load.
+//   - the block's cartridge staged in shared memory as bytes (16 KB for an
+//     F6 cartridge); an instruction's bytes are fetched as two aligned words
+//     joined by one funnel shift.
 // Instructions the hot switch does not take (BRK, RTI, JMP (ind), undocumented
 // opcodes, stack or pointer bytes outside RAM, fetches outside the cartridge
 // or next to a bank hotspot) run the general decoder out of line.
@@ -38,7 +39,6 @@ enum IoWord : uint32_t {
 };
 constexpr uint32_t IO_WSYNC = 1u, IO_VSYNC_RISE = 2u;
 
-__host__ __device__ constexpr uint32_t romw_mode(uint32_t w) { return (w >> 24) & 0xF; }
 
 // Shared-memory views of one env's TIA file and I/O state.
 struct IoCtx {
@@ -273,7 +273,7 @@ struct FastConsole;
 __device__ __forceinline__ void fc_exec_general(FastConsole *self);
 
 struct FastConsole {
-  const uint32_t *romw;    // staged cartridge words (banks of 4096)
+  const uint8_t *rom8;     // staged cartridge bytes (banks of 4096, then 16 bytes of padding)
   const uint8_t *dec_op;   // general decoder: opcode -> operation, then mode/cycles/penalty
   uint32_t *ram;           // &ram_block[env], stride E words
   IoCtx io;
@@ -418,6 +418,14 @@ struct FastConsole {
     if (fire && (io.T(T_VBLANK) & 0x40)) io.Sset(IO_LATCH, 1);
   }
 
+  // Cartridge bytes i .. i+3 of the stage, byte i lowest (i + 3 may run into
+  // the padding after the last bank).
+  __device__ __forceinline__ uint32_t fetch4(uint32_t i) const {
+    const uint32_t *r32 = reinterpret_cast<const uint32_t *>(rom8);
+    const uint32_t q = i >> 2;
+    return __funnelshift_r(r32[q], r32[q + 1], (i & 3u) * 8u);
+  }
+
   // ---- bus ----
   __device__ __forceinline__ void hotspot(uint32_t off) {
     if (scheme == 1) { if (off == 0xFF8 || off == 0xFF9) bank = off - 0xFF8; }
@@ -445,7 +453,7 @@ struct FastConsole {
     if (a & 0x1000) {
       const uint32_t off = a & 0xFFF;
       if (scheme) hotspot(off);
-      return romw[bank * 4096u + off] & 0xFF;
+      return rom8[bank * 4096u + off];
     }
     return fc_io_read(io, a, t);
   }
@@ -535,7 +543,7 @@ struct FastConsole {
   // Returns false (with nothing changed) for the cases the general decoder
   // takes.  Each case sets the cycle count n and the next PC; the tail
   // applies the WSYNC stall.
-  // w = the staged word at the current PC (bank * 4096 + (PC & 0xFFF)).
+  // w = cartridge bytes PC .. PC+3 of the current bank (fetch4).
   __device__ __forceinline__ bool exec(uint32_t w) {
     const uint32_t k0 = kf;
     const uint32_t pc = PC;
@@ -870,7 +878,7 @@ struct FastConsole {
     while (__any_sync(wmask, active)) {
       // next instruction word, fetched before the vote so the two latencies overlap
       // (bank < banks of the staged cartridge, so the index stays in the stage)
-      const uint32_t w = romw[bank * 4096u + (PC & 0xFFFu)];
+      const uint32_t w = fetch4(bank * 4096u + (PC & 0xFFFu));
       const uint32_t mine = active ? kf : 0xFFFFFFFFu;
       const uint32_t lead = __reduce_min_sync(wmask, mine);
       const uint32_t first = __ffs(__ballot_sync(wmask, active && kf == lead)) - 1;
