@@ -541,7 +541,7 @@ int build_groups(atari_env *E, int lanes, int warps) {
   E->n_groups = ng;
   E->lanes = lanes;
   E->warps = warps;
-  size_t smem = (size_t)E->rom_stage + 16 + 512 + (size_t)lanes * warps * (512 + 4 * IO_WORDS + TIA_BYTES);
+  size_t smem = (size_t)E->rom_stage + 16 + 512 + (size_t)lanes * warps * ENV_SMEM;
   int per_sm = 0;
   CUDA_TRY(cudaFuncSetAttribute(k_interp_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched, warps * 32, smem));
@@ -591,7 +591,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
 }
 
 size_t interp_smem(const atari_env *E) {
-  return (size_t)E->rom_stage + 16 + 512 + (size_t)E->lanes * E->warps * (512 + 4 * IO_WORDS + TIA_BYTES);
+  return (size_t)E->rom_stage + 16 + 512 + (size_t)E->lanes * E->warps * ENV_SMEM;
 }
 size_t fused_smem() { return 2 * 210 * 160 + 128 + 7056; }
 

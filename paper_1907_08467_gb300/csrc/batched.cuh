@@ -97,13 +97,13 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
       mt[1] = lines;
       log_total += nrec;
     }
-    const uint32_t s = m.ram[score * m.E];
+    const uint32_t s = m.ram[score];
     reward += (int32_t)(int8_t)(uint8_t)(s - score_prev);
     score_prev = s;
   }
   env_status |= m.all_status();
   if (m.jam) env_status |= ST_ILLEGAL;
-  const uint32_t done = (m.ram[gameover * m.E] != 0 || m.jam) ? 1u : 0u;
+  const uint32_t done = (m.ram[gameover] != 0 || m.jam) ? 1u : 0u;
   a.rew_int[i] = reward;
   a.done_int[i] = (uint8_t)done;
   if (a.rew_out) a.rew_out[o] = reward;
@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
   uint8_t *rom8 = smem;                                  // rom_stage bytes, then 16 of padding
   uint8_t *dec_op = smem + (size_t)a.rom_stage + 16;
   uint32_t *ram = reinterpret_cast<uint32_t *>(dec_op + 512);
-  uint32_t *iow = ram + 128 * a.E;
-  uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_WORDS * a.E);
+  uint32_t *iow = ram + RAM_STRIDE * a.E;
+  uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_STRIDE * a.E);
   __shared__ int s_group;
   for (int t = threadIdx.x; t < 512; t += blockDim.x) dec_op[t] = a.dec_op[t];
   int cur_rom = -1;
@@ -165,9 +165,8 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
         FastConsole m;
         m.rom8 = rom8;
         m.dec_op = dec_op;
-        m.ram = ram + j;
-        m.io = IoCtx{tia + j, iow + j, (uint32_t)a.E};
-        m.E = (uint32_t)a.E;
+        m.ram = ram + RAM_STRIDE * j;
+        m.io = IoCtx{tia + TIA_STRIDE * j, iow + IO_STRIDE * j};
         m.scheme = inf & 0xFF;
         m.wmask = wmask;
         m.load(st);

@@ -2,16 +2,14 @@
 //
 // Same machine and canonical state as Console in device_machine.cuh:
 //   - the hot loop is a single switch on the opcode byte; every case has its
-//     addressing mode and cycle count folded in, so an emulated instruction
-//     costs one shared-memory fetch, one indirect branch and its own work;
+//     addressing mode and cycle count folded in;
 //   - CPU registers (flags split, N and Z kept as the last result byte),
 //     the cycle counter and the bank in registers;
-//   - RAM in shared memory, one 32-bit word per byte, interleaved by env
-//     (word = address * E + env): a warp's RAM accesses never bank-conflict;
-//   - the TIA register file (bytes) and the I/O state (collision cursor and
-//     latches, RIOT timer and ports, inputs, log cursor, frame base line)
-//     in shared memory, interleaved the same way, touched only by the
-//     out-of-line I/O functions below;
+//   - RAM (one 32-bit word per byte), the TIA register file (bytes) and the
+//     I/O state (collision cursor and latches, RIOT timer and ports, inputs,
+//     log cursor, frame base line) in shared memory, one block per env with
+//     odd word strides, so lanes reading the same field never bank-conflict
+//     and every access is a base pointer plus an offset;
 //   - the block's cartridge staged in shared memory as bytes (16 KB for an
 //     F6 cartridge); an instruction's bytes are fetched as two aligned words
 //     joined by one funnel shift.
@@ -25,7 +23,6 @@
 
 namespace atari {
 
-constexpr uint32_t TIA_BYTES = 40;  // shared-memory bytes per env for the TIA file (37 used)
 enum TiaSlot : uint32_t {
   T_VSYNC = 0, T_VBLANK, T_NUSIZ0, T_NUSIZ1, T_COLUP0, T_COLUP1, T_COLUPF, T_COLUBK, T_CTRLPF, T_REFP0,
   T_REFP1, T_PF0, T_PF1, T_PF2, T_ENAM0, T_ENAM1, T_ENABL_N, T_ENABL_O, T_GRP0_N, T_GRP0_O, T_GRP1_N,
@@ -40,21 +37,26 @@ enum IoWord : uint32_t {
 constexpr uint32_t IO_WSYNC = 1u, IO_VSYNC_RISE = 2u;
 
 
+// Per-env blocks of shared memory, env-major, with strides chosen so that a
+// warp's lanes touching the same field hit 32 different banks: RAM one word
+// per byte (129 words per env), I/O state 19 words, TIA file 44 bytes (11
+// words).  Every access is the lane's base plus a constant or one add.
+constexpr uint32_t RAM_STRIDE = 129, IO_STRIDE = IO_WORDS, TIA_STRIDE = 44;
+static_assert(IO_STRIDE % 2 == 1 && (TIA_STRIDE / 4) % 2 == 1 && RAM_STRIDE % 2 == 1, "odd word strides");
+constexpr uint32_t ENV_SMEM = 4 * RAM_STRIDE + 4 * IO_STRIDE + TIA_STRIDE;
+
 // Shared-memory views of one env's TIA file and I/O state.
 struct IoCtx {
   uint8_t *tia;
   uint32_t *io;
-  uint32_t E;
-  __device__ __forceinline__ uint32_t T(uint32_t s) const { return tia[s * E]; }
-  __device__ __forceinline__ void Tset(uint32_t s, uint32_t v) const { tia[s * E] = (uint8_t)v; }
-  __device__ __forceinline__ uint32_t G(uint32_t w) const { return io[w * E]; }
-  __device__ __forceinline__ void Sset(uint32_t w, uint32_t v) const { io[w * E] = v; }
-  __device__ __forceinline__ uint64_t G64(uint32_t w) const {
-    return (uint64_t)io[w * E] | (uint64_t)io[(w + 1) * E] << 32;
-  }
+  __device__ __forceinline__ uint32_t T(uint32_t s) const { return tia[s]; }
+  __device__ __forceinline__ void Tset(uint32_t s, uint32_t v) const { tia[s] = (uint8_t)v; }
+  __device__ __forceinline__ uint32_t G(uint32_t w) const { return io[w]; }
+  __device__ __forceinline__ void Sset(uint32_t w, uint32_t v) const { io[w] = v; }
+  __device__ __forceinline__ uint64_t G64(uint32_t w) const { return (uint64_t)io[w] | (uint64_t)io[w + 1] << 32; }
   __device__ __forceinline__ void S64(uint32_t w, uint64_t v) const {
-    io[w * E] = (uint32_t)v;
-    io[(w + 1) * E] = (uint32_t)(v >> 32);
+    io[w] = (uint32_t)v;
+    io[w + 1] = (uint32_t)(v >> 32);
   }
 };
 
@@ -275,9 +277,8 @@ __device__ __forceinline__ void fc_exec_general(FastConsole *self);
 struct FastConsole {
   const uint8_t *rom8;     // staged cartridge bytes (banks of 4096, then 16 bytes of padding)
   const uint8_t *dec_op;   // general decoder: opcode -> operation, then mode/cycles/penalty
-  uint32_t *ram;           // &ram_block[env], stride E words
+  uint32_t *ram;           // this env's RAM block, one word per byte
   IoCtx io;
-  uint32_t E;
   uint32_t A, X, Y, SP, PC, fc, fv, fn, fz, fdi;  // fdi holds the D (0x08) and I (0x04) bits
   uint32_t bank, jam, scheme;
   uint32_t kf;             // CPU cycles since the first line of the frame
@@ -330,7 +331,7 @@ struct FastConsole {
       const uint4 v = r4[q];
       const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int b = 0; b < 16; ++b) ram[(q * 16 + b) * E] = (ws[b >> 2] >> (8 * (b & 3))) & 0xFF;
+      for (int b = 0; b < 16; ++b) ram[q * 16 + b] = (ws[b >> 2] >> (8 * (b & 3))) & 0xFF;
     }
     status = 0; instret = 0; pend = 0; vs_kf = ~0u;
   }
@@ -365,7 +366,7 @@ struct FastConsole {
       for (int k2 = 0; k2 < 4; ++k2) {
         uint32_t v = 0;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) v |= (ram[(q * 16 + k2 * 4 + b) * E] & 0xFF) << (8 * b);
+        for (int b = 0; b < 4; ++b) v |= (ram[q * 16 + k2 * 4 + b] & 0xFF) << (8 * b);
         ws[k2] = v;
       }
       r4[q] = make_uint4(ws[0], ws[1], ws[2], ws[3]);
@@ -436,11 +437,11 @@ struct FastConsole {
   }
   // zero-page access: RAM for $80-$FF, TIA below
   __device__ __forceinline__ uint32_t rdz(uint32_t z, uint32_t t) {
-    return (z & 0x80) ? ram[(z & 0x7F) * E] : fc_io_read(io, z, t);
+    return (z & 0x80) ? ram[z & 0x7F] : fc_io_read(io, z, t);
   }
   __device__ __forceinline__ void wrz(uint32_t z, uint32_t v, uint32_t t) {
     if (z & 0x80) {
-      ram[(z & 0x7F) * E] = v & 0xFF;
+      ram[z & 0x7F] = v & 0xFF;
     } else {
       const uint32_t f = fc_io_write(io, z, v & 0xFF, t);
       pend |= f;
@@ -449,7 +450,7 @@ struct FastConsole {
   }
   __device__ __forceinline__ uint32_t rd(uint32_t addr, uint32_t t) {
     const uint32_t a = addr & 0x1FFF;
-    if ((a & 0x1280) == 0x0080) return ram[(a & 0x7F) * E];
+    if ((a & 0x1280) == 0x0080) return ram[a & 0x7F];
     if (a & 0x1000) {
       const uint32_t off = a & 0xFFF;
       if (scheme) hotspot(off);
@@ -459,7 +460,7 @@ struct FastConsole {
   }
   __device__ __forceinline__ void wr(uint32_t addr, uint32_t v, uint32_t t) {
     const uint32_t a = addr & 0x1FFF;
-    if ((a & 0x1280) == 0x0080) { ram[(a & 0x7F) * E] = v & 0xFF; return; }
+    if ((a & 0x1280) == 0x0080) { ram[a & 0x7F] = v & 0xFF; return; }
     if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
     const uint32_t f = fc_io_write(io, a, v & 0xFF, t);
     pend |= f;
@@ -471,7 +472,7 @@ struct FastConsole {
   // TIA or RIOT address through the out-of-line writer.
   __device__ __forceinline__ void bus_store(uint32_t addr, uint32_t v, uint32_t t) {
     const uint32_t a = addr & 0x1FFF;
-    if ((a & 0x1280) == 0x0080) { ram[(a & 0x7F) * E] = v & 0xFF; return; }
+    if ((a & 0x1280) == 0x0080) { ram[a & 0x7F] = v & 0xFF; return; }
     if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
     if (!(a & 0x80)) {
       const uint32_t reg = a & 0x3F;
@@ -571,10 +572,10 @@ struct FastConsole {
   case OPAY: { const uint32_t ea = ABY_; n = 4 + XPG(a16, ea); const uint32_t v = rd(ea, k0 + n - 1); BODY;   \
                PC = pc + 3; break; }                                                                          \
   case OPIX: { const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;                          \
-               const uint32_t ea = ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8;                      \
+               const uint32_t ea = ram[z & 0x7F] | ram[(z + 1) & 0x7F] << 8;                      \
                const uint32_t v = rd(ea, k0 + 5); BODY; n = 6; PC = pc + 2; break; }                           \
   case OPIY: { if (!(b1 & 0x80) || b1 == 0xFF) return false;                                                  \
-               const uint32_t base = ram[(b1 & 0x7F) * E] | ram[((b1 + 1) & 0x7F) * E] << 8;                  \
+               const uint32_t base = ram[b1 & 0x7F] | ram[(b1 + 1) & 0x7F] << 8;                  \
                const uint32_t ea = (base + Y) & 0xFFFF; n = 5 + XPG(base, ea);                                \
                const uint32_t v = rd(ea, k0 + n - 1); BODY; PC = pc + 2; break; }
 // read-modify-write: acc, zp, zp,X, abs, abs,X
@@ -643,9 +644,9 @@ struct FastConsole {
       case 0x9D: sa = ABX_; sv = A; stc = k0 + 4; n = 5; PC = pc + 3; break;
       case 0x99: sa = ABY_; sv = A; stc = k0 + 4; n = 5; PC = pc + 3; break;
       case 0x81: { const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;
-                   sa = ram[(z & 0x7F) * E] | ram[((z + 1) & 0x7F) * E] << 8; sv = A; stc = k0 + 5; n = 6; PC = pc + 2; break; }
+                   sa = ram[z & 0x7F] | ram[(z + 1) & 0x7F] << 8; sv = A; stc = k0 + 5; n = 6; PC = pc + 2; break; }
       case 0x91: { if (!(b1 & 0x80) || b1 == 0xFF) return false;
-                   const uint32_t base = ram[(b1 & 0x7F) * E] | ram[((b1 + 1) & 0x7F) * E] << 8;
+                   const uint32_t base = ram[b1 & 0x7F] | ram[(b1 + 1) & 0x7F] << 8;
                    sa = (base + Y) & 0xFFFF; sv = A; stc = k0 + 5; n = 6; PC = pc + 2; break; }
       case 0x86: sa = b1; sv = X; stc = k0 + 2; n = 3; PC = pc + 2; break;
       case 0x96: sa = ZPY_; sv = X; stc = k0 + 3; n = 4; PC = pc + 2; break;
@@ -685,20 +686,20 @@ struct FastConsole {
       IMPL(0xD8, { fdi &= ~0x08u; })
       IMPL(0xF8, { fdi |= 0x08u; })
       IMPL(0xEA, {})
-      case 0x48: if (!(SP & 0x80)) return false; ram[(SP & 0x7F) * E] = A; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
-      case 0x08: if (!(SP & 0x80)) return false; ram[(SP & 0x7F) * E] = P() | 0x10u; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
+      case 0x48: if (!(SP & 0x80)) return false; ram[SP & 0x7F] = A; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
+      case 0x08: if (!(SP & 0x80)) return false; ram[SP & 0x7F] = P() | 0x10u; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
       case 0x68: { const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
-                   SP = s1; A = ram[(s1 & 0x7F) * E]; NZ(A); n = 4; PC = pc + 1; break; }
+                   SP = s1; A = ram[s1 & 0x7F]; NZ(A); n = 4; PC = pc + 1; break; }
       case 0x28: { const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
-                   SP = s1; setP(ram[(s1 & 0x7F) * E]); n = 4; PC = pc + 1; break; }
+                   SP = s1; setP(ram[s1 & 0x7F]); n = 4; PC = pc + 1; break; }
       case 0x4C: PC = a16; n = 3; break;
       case 0x20: { if (SP < 0x81) return false;
                    const uint32_t ret = (pc + 2) & 0xFFFF;
-                   ram[(SP & 0x7F) * E] = ret >> 8; ram[((SP - 1) & 0x7F) * E] = ret & 0xFF;
+                   ram[SP & 0x7F] = ret >> 8; ram[(SP - 1) & 0x7F] = ret & 0xFF;
                    SP = (SP - 2) & 0xFF; PC = a16; n = 6; break; }
       case 0x60: { const uint32_t s1 = (SP + 1) & 0xFF, s2 = (SP + 2) & 0xFF;
                    if (!(s1 & 0x80) || !(s2 & 0x80)) return false;
-                   PC = ((ram[(s1 & 0x7F) * E] | ram[(s2 & 0x7F) * E] << 8) + 1) & 0xFFFF; SP = s2; n = 6; break; }
+                   PC = ((ram[s1 & 0x7F] | ram[s2 & 0x7F] << 8) + 1) & 0xFFFF; SP = s2; n = 6; break; }
       default: return false;  // BRK, RTI, JMP (ind), undocumented
     }
 #undef ZPX_
