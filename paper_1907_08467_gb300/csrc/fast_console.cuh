@@ -45,18 +45,22 @@ constexpr uint32_t RAM_STRIDE = 129, IO_STRIDE = IO_WORDS, TIA_STRIDE = 44;
 static_assert(IO_STRIDE % 2 == 1 && (TIA_STRIDE / 4) % 2 == 1 && RAM_STRIDE % 2 == 1, "odd word strides");
 constexpr uint32_t ENV_SMEM = 4 * RAM_STRIDE + 4 * IO_STRIDE + TIA_STRIDE;
 
-// Shared-memory views of one env's TIA file and I/O state.
+// Shared-memory views of one env's TIA file and I/O state.  The pointers
+// reach the out-of-line I/O functions as plain pointers; the assumption lets
+// the compiler address them as shared memory there too.
 struct IoCtx {
   uint8_t *tia;
   uint32_t *io;
-  __device__ __forceinline__ uint32_t T(uint32_t s) const { return tia[s]; }
-  __device__ __forceinline__ void Tset(uint32_t s, uint32_t v) const { tia[s] = (uint8_t)v; }
-  __device__ __forceinline__ uint32_t G(uint32_t w) const { return io[w]; }
-  __device__ __forceinline__ void Sset(uint32_t w, uint32_t v) const { io[w] = v; }
-  __device__ __forceinline__ uint64_t G64(uint32_t w) const { return (uint64_t)io[w] | (uint64_t)io[w + 1] << 32; }
-  __device__ __forceinline__ void S64(uint32_t w, uint64_t v) const {
-    io[w] = (uint32_t)v;
-    io[w + 1] = (uint32_t)(v >> 32);
+  __device__ __forceinline__ uint8_t *t() const { __builtin_assume(__isShared(tia)); return tia; }
+  __device__ __forceinline__ uint32_t *w() const { __builtin_assume(__isShared(io)); return io; }
+  __device__ __forceinline__ uint32_t T(uint32_t s) const { return t()[s]; }
+  __device__ __forceinline__ void Tset(uint32_t s, uint32_t v) const { t()[s] = (uint8_t)v; }
+  __device__ __forceinline__ uint32_t G(uint32_t i) const { return w()[i]; }
+  __device__ __forceinline__ void Sset(uint32_t i, uint32_t v) const { w()[i] = v; }
+  __device__ __forceinline__ uint64_t G64(uint32_t i) const { return (uint64_t)w()[i] | (uint64_t)w()[i + 1] << 32; }
+  __device__ __forceinline__ void S64(uint32_t i, uint64_t v) const {
+    w()[i] = (uint32_t)v;
+    w()[i + 1] = (uint32_t)(v >> 32);
   }
 };
 
@@ -903,13 +907,17 @@ struct FastConsole {
   }
 };
 
-// Out-of-line general instruction on a copy of the register state (the
-// caller's console stays in registers).
+// Out-of-line general instruction on a copy of the console.  Only the CPU
+// and timing state comes back: the caller's pointers into shared memory are
+// never reloaded from the copy, so they keep their shared address space.
 __device__ __noinline__ void fc_exec_general_impl(FastConsole *c) { c->exec_general(); }
 __device__ __forceinline__ void fc_exec_general(FastConsole *self) {
   FastConsole tmp = *self;
   fc_exec_general_impl(&tmp);
-  *self = tmp;
+  self->A = tmp.A; self->X = tmp.X; self->Y = tmp.Y; self->SP = tmp.SP; self->PC = tmp.PC;
+  self->fc = tmp.fc; self->fv = tmp.fv; self->fn = tmp.fn; self->fz = tmp.fz; self->fdi = tmp.fdi;
+  self->bank = tmp.bank; self->jam = tmp.jam; self->kf = tmp.kf; self->pend = tmp.pend; self->vs_kf = tmp.vs_kf;
+  self->status = tmp.status; self->instret = tmp.instret; self->frame_no = tmp.frame_no;
 }
 
 }  // namespace atari
