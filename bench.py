@@ -71,15 +71,28 @@ def parse():
     return p.parse_args()
 
 
-def dist_setup():
+_REDUCE_DEVICE = "cuda"
+
+
+def dist_setup(backend: str = "nccl"):
+    """Replicas: one process per GPU from torchrun's environment.  Only the
+    timing and the whole-job frame count cross ranks (no collective touches
+    the emulation path)."""
+    global _REDUCE_DEVICE
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    _REDUCE_DEVICE = "cuda" if backend == "nccl" else "cpu"
     if ws > 1:
         import torch.distributed as dist
-        backend = "nccl"
         dist.init_process_group(backend)
     return ws, rank, local
+
+
+def replica_env_keys(n_envs: int, rank: int):
+    """Env keys of a rank's replica of the workload: disjoint across ranks."""
+    import numpy as np
+    return np.arange(n_envs, dtype=np.uint32) + np.uint32(rank * n_envs)
 
 
 def barrier(ws):
@@ -93,7 +106,7 @@ def allreduce_max(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_REDUCE_DEVICE)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -103,7 +116,7 @@ def allreduce_sum(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=_REDUCE_DEVICE)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
@@ -317,7 +330,7 @@ def main():
     torch.cuda.set_device(local)
     form = FORM_BATCHED if args.form == "batched" else FORM_PLAIN
     # replicas: each rank runs the whole workload with its own env keys
-    env_key = np.arange(w.n_envs, dtype=np.uint32) + np.uint32(rank * w.n_envs)
+    env_key = replica_env_keys(w.n_envs, rank)
     env = AtariEnv([r.data for r in w.roms], [(r.score_addr, r.gameover_addr) for r in w.roms], w.env_rom,
                    luma=synth.luma_table(), env_key=env_key, frameskip=w.frameskip, sticky=w.sticky,
                    output_mode=w.output_mode, form=form, seed=w.seed, envs_per_warp=args.envs_per_warp,

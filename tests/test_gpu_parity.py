@@ -274,3 +274,27 @@ def test_state_with_extra_bank_bits_matches_oracle(form):
     assert_same("dones", done.cpu().numpy(), od)
     assert_same("obs", obs.cpu().numpy(), oo)
     run_parity(g, o, acts[2:])
+
+
+def test_full_size_banked_config_sampled():
+    """The 32768-env, 32-cartridge banked configuration with sticky actions
+    in the benchmark's launch configuration (autotuned batched form): 10
+    steps, no env faults, and 48 sampled envs (3 of every other cartridge,
+    own env keys) equal to the oracle run on just those envs."""
+    w = synth.workload(3)
+    n = w.n_envs
+    g = AtariEnv.from_workload(w, form=FORM_BATCHED)
+    rng = np.random.default_rng(31)
+    idx = np.sort(np.concatenate([rng.choice(np.flatnonzero(np.asarray(w.env_rom) == r), 3, replace=False)
+                                  for r in range(0, 32, 2)]))
+    o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
+                   [w.env_rom[i] for i in idx], luma=synth.luma_table(), env_key=idx, sticky=True, seed=w.seed)
+    acts = synth.actions(33, 10, n)
+    for s in range(10):
+        obs, rew, done = g.step(torch.from_numpy(acts[s]).cuda())
+        oo, orw, od = o.step(acts[s][idx], n_threads=8)
+        assert_same(f"step {s} rewards", rew.cpu().numpy()[idx], orw)
+        assert_same(f"step {s} dones", done.cpu().numpy()[idx], od)
+        assert_same(f"step {s} obs", obs.cpu().numpy()[idx], oo)
+    assert_same("state", g.state().cpu().numpy()[idx], o.state())
+    assert int(g.status().abs().sum().item()) == 0
