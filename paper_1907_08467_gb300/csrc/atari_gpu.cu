@@ -451,6 +451,7 @@ struct atari_env {
   uint8_t *d_cache = nullptr;
   uint32_t *d_log = nullptr;
   uint8_t *d_snap = nullptr;
+  uint8_t *d_bsnap = nullptr;   // batched stack form: [n][2][3][64] band start snapshots
   uint32_t *d_meta = nullptr;
   uint8_t *d_frames = nullptr;
   uint8_t *d_ring = nullptr;
@@ -569,6 +570,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
   a.done_out = d_dones;
   a.log = E->d_log;
   a.snap = E->d_snap;
+  a.bsnap = E->d_bsnap;
   a.meta = E->d_meta;
   a.counters = E->d_ctr;
   a.grp_rom = E->d_grp;
@@ -665,6 +667,7 @@ size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg) {
   if (cfg->form == ATARI_FORM_PLAIN) b += n * 2 * 210 * 160;   // frames (plain form only)
   else b += (size_t)n_roms * 16384 + 512 + n * 4 + 64;         // cartridge bytes for the stage, work items
   if (cfg->output_mode == ATARI_OUT_STACK) b += n * 4 * 7056 + n;
+  if (cfg->output_mode == ATARI_OUT_STACK && cfg->form == ATARI_FORM_BATCHED) b += n * 2 * 3 * 64;  // band snapshots
   b += n * (4 + 1 + 8 + 1);                               // rewards, dones, counters, action staging
   return b;
 }
@@ -714,6 +717,7 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
     return bail(rc);
   if (c.output_mode == ATARI_OUT_STACK) {
     if ((rc = dalloc(&E->d_ring, n * 4 * 7056, T)) || (rc = dalloc(&E->d_head, n, T))) return bail(rc);
+    if (c.form == ATARI_FORM_BATCHED && (rc = dalloc(&E->d_bsnap, n * 2 * 3 * 64, T))) return bail(rc);
   }
 
   // cartridges: 2K images mirrored to 4K, each in a 16 KB slot
@@ -793,7 +797,7 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
 void atari_env_destroy(atari_env *E) {
   if (!E) return;
   void *ptrs[] = {E->d_roms, E->d_info, E->d_dec, E->d_env_rom, E->d_env_key, E->d_state, E->d_cache, E->d_log,
-                  E->d_snap, E->d_meta, E->d_frames, E->d_ring, E->d_head, E->d_luma, E->d_rew, E->d_done,
+                  E->d_snap, E->d_bsnap, E->d_meta, E->d_frames, E->d_ring, E->d_head, E->d_luma, E->d_rew, E->d_done,
                   E->d_ctr, E->d_act, E->d_obs_tmp, E->d_romb, E->d_dec_op, E->d_grp, E->d_queue};
   for (auto &g : E->graphs) cudaGraphExecDestroy(g.exec);
   if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
@@ -887,7 +891,7 @@ int launch_batched(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
   CUDA_TRY(cudaGetLastError());
   if (c.output_mode == ATARI_OUT_STACK) {
     ProfScope p(E, ATARI_PROF_FUSED, s);
-    k_raster_preprocess<<<E->n, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma, E->d_ring,
+    k_raster_preprocess<<<E->n, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma, E->d_ring,
                                                                 E->d_head, E->d_done, d_obs, E->n, c.log_cap, E->wpf, nullptr, nullptr);
   } else if (d_obs) {
     ProfScope p(E, ATARI_PROF_RASTER, s);
@@ -987,7 +991,7 @@ int autotune(atari_env *E) {
         float t = 0;
         for (int rep = 0; rep < 2; ++rep) {
           cudaEventRecord(e0);
-          k_raster_preprocess<<<E->n, 64 * wpf, fused_smem()>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma, E->d_ring,
+          k_raster_preprocess<<<E->n, 64 * wpf, fused_smem()>>>(E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma, E->d_ring,
                                                                E->d_head, E->d_done, nullptr, E->n, E->cfg.log_cap, wpf, nullptr, nullptr);
           cudaEventRecord(e1);
           cudaEventSynchronize(e1);
@@ -1447,7 +1451,7 @@ int serve_tick(atari_env *E, const ServeTick &t, cudaStream_t s) {
   const int grid = std::max(1, std::min(t.n_groups, E->max_blocks));
   k_interp_batched<<<grid, E->warps * 32, interp_smem(E), s>>>(a);
   CUDA_TRY(cudaGetLastError());
-  k_raster_preprocess<<<t.n_active, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_meta, E->d_luma,
+  k_raster_preprocess<<<t.n_active, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma,
                                                                    E->d_ring, E->d_head, E->d_done, t.d_obs,
                                                                    t.n_active, c.log_cap, E->wpf, a.perm, a.opos);
   CUDA_TRY(cudaGetLastError());

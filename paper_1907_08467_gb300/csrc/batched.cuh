@@ -35,6 +35,7 @@ struct BatchArgs {
   uint8_t *done_out;
   uint32_t *log;
   uint8_t *snap;
+  uint8_t *bsnap;            // null, or [n][2][3][64] quarter-frame band start snapshots
   uint32_t *meta;
   uint32_t *counters;
   const int32_t *grp_rom, *grp_start, *grp_count, *perm;
@@ -85,12 +86,14 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
     const bool logging = slot >= a.first_slot;
     if (logging) {
       m.snapshot(a.snap + ((size_t)i * 2 + slot) * 64);
-      m.set_log(a.log + ((size_t)i * 2 + slot) * a.log_cap, (uint32_t)a.log_cap);
+      m.set_log(a.log + ((size_t)i * 2 + slot) * a.log_cap, (uint32_t)a.log_cap,
+                a.bsnap ? a.bsnap + ((size_t)i * 2 + slot) * 3 * 64 : nullptr);
     } else {
-      m.set_log(nullptr, 0);
+      m.set_log(nullptr, 0, nullptr);
     }
     const uint32_t lines = m.run_frame();
     if (logging) {
+      m.finish_bands();
       uint32_t *mt = a.meta + ((size_t)i * 2 + slot) * 2;
       const uint32_t nrec = m.log_count();
       mt[0] = nrec;
@@ -177,11 +180,13 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
 }
 
 // Render rows [r0, r1) of one frame with one warp into a shared-memory frame.
+// R holds the render state after records [0, ri0); records from ri0 on that
+// take effect before the band's first row are applied first.
 __device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uint32_t n_rec, uint32_t n_lines,
-                                        uint32_t r0, uint32_t r1, uint8_t *frame) {
+                                        uint32_t r0, uint32_t r1, uint8_t *frame, uint32_t ri0) {
   const uint32_t lane = threadIdx.x & 31;
-  uint32_t ri = 0, base = 0;
-  uint32_t chunk = lane < n_rec ? recs[lane] : 0xFFFFFFFFu;
+  uint32_t ri = ri0, base = ri0;
+  uint32_t chunk = base + lane < n_rec ? recs[base + lane] : 0xFFFFFFFFu;
   // records that take effect before the band's first row: apply only
   const uint32_t start_clk = 228u * (WINDOW_Y0 + r0);
   while (ri < n_rec) {
@@ -228,7 +233,8 @@ __device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uin
 
 // One block per env: warps [0, W) render frame F-1, warps [W, 2W) frame F,
 // each warp a band of rows; then luma max, 84x84 area resampling, stack push.
-__global__ void __launch_bounds__(256) k_raster_preprocess(const uint32_t *log, const uint8_t *snap, const uint32_t *meta,
+__global__ void __launch_bounds__(256) k_raster_preprocess(const uint32_t *log, const uint8_t *snap, const uint8_t *bsnap,
+                                                           const uint32_t *meta,
                                                            const uint8_t *luma_g, uint8_t *ring, uint8_t *head,
                                                            const uint8_t *done, uint8_t *obs, int n, int log_cap,
                                                            int warps_per_frame, const int32_t *perm,
@@ -249,11 +255,22 @@ __global__ void __launch_bounds__(256) k_raster_preprocess(const uint32_t *log, 
     const uint32_t r0 = (uint32_t)(FRAME_H * band / warps_per_frame);
     const uint32_t r1 = (uint32_t)(FRAME_H * (band + 1) / warps_per_frame);
     const size_t fs = (size_t)i * 2 + slot;
-    RenderRegs R;
-    R.load(snap + fs * 64);
     const uint32_t *mt = meta + fs * 2;
     const uint32_t n_rec = mt[0] < (uint32_t)log_cap ? mt[0] : (uint32_t)log_cap;
-    render_rows_warp(R, log + fs * log_cap, n_rec, mt[1], r0, r1, slot ? fb : fa);
+    // a band starting at a quarter of the frame starts from the interpreter's
+    // snapshot there; the first band from the frame's start
+    const uint32_t q = (uint32_t)(band * 4 / warps_per_frame);
+    RenderRegs R;
+    uint32_t ri0 = 0;
+    if (bsnap && q > 0 && (band * 4) % warps_per_frame == 0) {
+      const uint8_t *bs = bsnap + (fs * 3 + q - 1) * 64;
+      R.load(bs);
+      ri0 = reinterpret_cast<const uint32_t *>(bs)[14];
+      ri0 = ri0 < n_rec ? ri0 : n_rec;
+    } else {
+      R.load(snap + fs * 64);
+    }
+    render_rows_warp(R, log + fs * log_cap, n_rec, mt[1], r0, r1, slot ? fb : fa, ri0);
   }
   __syncthreads();
   {

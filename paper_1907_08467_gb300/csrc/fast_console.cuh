@@ -32,7 +32,10 @@ enum TiaSlot : uint32_t {
 // I/O state words (shared memory, interleaved by env)
 enum IoWord : uint32_t {
   IO_CEVAL = 0, IO_CX, IO_L0LO, IO_L0HI, IO_BARLO, IO_BARHI, IO_TCWLO, IO_TCWHI, IO_TV, IO_TSH, IO_PORTS,
-  IO_JOY, IO_FIRE, IO_LATCH, IO_LOGLO, IO_LOGHI, IO_LOGN, IO_LOGCAP, IO_STATUS, IO_WORDS
+  IO_JOY, IO_FIRE, IO_LATCH, IO_LOGLO, IO_LOGHI, IO_LOGN, IO_LOGCAP, IO_STATUS,
+  IO_BANDN,      // next quarter-frame band whose start snapshot is due (1..3), 4: none
+  IO_BSLO, IO_BSHI,  // where this frame's band snapshots go (3 x 64 bytes)
+  IO_PAD, IO_WORDS
 };
 constexpr uint32_t IO_WSYNC = 1u, IO_VSYNC_RISE = 2u;
 
@@ -176,11 +179,50 @@ __device__ __noinline__ uint32_t fc_io_read(IoCtx c, uint32_t a, uint32_t t) {
   return (uint32_t)(0xFFull - (n - span)) & 0xFF;
 }
 
+// 64-byte render snapshot: TIA file (canonical bytes 0x20..0x44), HMOVE bar
+// line, frame base line; word 14 = the number of log records before it.
+__device__ __forceinline__ void fc_snapshot(IoCtx c, uint8_t *o, uint32_t nrec) {
+  uint32_t v[16];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    uint32_t x = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+      if (q * 4 + b < 37) x |= c.T(q * 4 + b) << (8 * b);
+    v[q] = x;
+  }
+  v[9] &= 0xFFu;
+  v[10] = c.G(IO_BARLO); v[11] = c.G(IO_BARHI);
+  v[12] = c.G(IO_L0LO); v[13] = c.G(IO_L0HI);
+  v[14] = nrec; v[15] = 0;
+  uint4 *d = reinterpret_cast<uint4 *>(o);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) d[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// First color clock of quarter-frame band q (rows 210 q / 4 of the window).
+__device__ __forceinline__ uint32_t fc_band_clk(uint32_t q) { return 228u * (WINDOW_Y0 + (FRAME_H * q) / 4u); }
+
+// Snapshot the render state at the start of every band due by clock eff: the
+// state after all records of earlier clocks, so the rasteriser's warps start
+// their bands there instead of replaying the frame from its first record.
+__device__ __noinline__ void fc_band_snap(IoCtx c, uint32_t eff) {
+  uint32_t bn = c.G(IO_BANDN);
+  uint8_t *base = reinterpret_cast<uint8_t *>((uint64_t)c.G(IO_BSLO) | (uint64_t)c.G(IO_BSHI) << 32);
+  const uint32_t nrec = c.G(IO_LOGN);
+  while (bn < 4 && eff >= fc_band_clk(bn)) {
+    fc_snapshot(c, base + (bn - 1) * 64, nrec);
+    ++bn;
+  }
+  c.Sset(IO_BANDN, bn);
+}
+
 // Append one TIA write record (effect clock, register, value) to the log of
 // a rendered frame.
 __device__ __forceinline__ void fc_log(IoCtx c, uint32_t eff, uint32_t reg, uint32_t v) {
   const uint32_t lo = c.G(IO_LOGLO), hi = c.G(IO_LOGHI);
   if (lo | hi) {
+    if (c.G(IO_BANDN) < 4 && eff >= fc_band_clk(c.G(IO_BANDN))) fc_band_snap(c, eff);
     uint32_t *lp = reinterpret_cast<uint32_t *>((uint64_t)lo | (uint64_t)hi << 32);
     const uint32_t nrec = c.G(IO_LOGN);
     if (nrec < c.G(IO_LOGCAP)) lp[nrec] = eff << 14 | reg << 8 | v;
@@ -376,29 +418,21 @@ struct FastConsole {
       r4[q] = make_uint4(ws[0], ws[1], ws[2], ws[3]);
     }
   }
-  __device__ void snapshot(uint8_t *o) const {
-    uint32_t v[16];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) {
-      uint32_t x = 0;
-#pragma unroll
-      for (int b = 0; b < 4; ++b)
-        if (q * 4 + b < 37) x |= io.T(q * 4 + b) << (8 * b);
-      v[q] = x;
-    }
-    v[9] &= 0xFFu;
-    v[10] = io.G(IO_BARLO); v[11] = io.G(IO_BARHI);
-    v[12] = io.G(IO_L0LO); v[13] = io.G(IO_L0HI);
-    v[14] = 0; v[15] = 0;
-    uint4 *d = reinterpret_cast<uint4 *>(o);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) d[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-  }
-  __device__ void set_log(uint32_t *p, uint32_t cap) {
+  __device__ void snapshot(uint8_t *o) const { fc_snapshot(io, o, 0); }
+  // Log the frame's TIA writes to p (cap records); bands: where the three
+  // quarter-frame start snapshots go, or null for none.
+  __device__ void set_log(uint32_t *p, uint32_t cap, uint8_t *bands) {
     io.Sset(IO_LOGLO, (uint32_t)(uint64_t)p);
     io.Sset(IO_LOGHI, (uint32_t)((uint64_t)p >> 32));
     io.Sset(IO_LOGN, 0);
     io.Sset(IO_LOGCAP, cap);
+    io.Sset(IO_BANDN, bands ? 1u : 4u);
+    io.Sset(IO_BSLO, (uint32_t)(uint64_t)bands);
+    io.Sset(IO_BSHI, (uint32_t)((uint64_t)bands >> 32));
+  }
+  // Band starts the frame never reached take its final state.
+  __device__ void finish_bands() {
+    if (io.G(IO_BANDN) < 4) fc_band_snap(io, ~0u);
   }
   __device__ uint32_t log_count() const { return io.G(IO_LOGN); }
   __device__ uint32_t all_status() const { return status | io.G(IO_STATUS); }
