@@ -227,7 +227,9 @@ __device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uin
       ++ri;
     }
     R.prepare(k < 5, lane);
-    for (; k < 5; ++k) row[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
+    if (__all_sync(0xFFFFFFFFu, k == 0)) R.row5(lane, line, row);
+    else
+      for (; k < 5; ++k) row[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
   }
 }
 

@@ -128,6 +128,34 @@ struct RenderRegs {
   __device__ __forceinline__ void prepare(bool draws, uint32_t lane) {
     if (__any_sync(0xFFFFFFFFu, draws && dirty != 0)) refresh(lane);
   }
+  // All five pixels of the lane on a line drawn from one register state
+  // (no write lands between them): pixel_k for k = 0..4 with the blanking
+  // and priority tests taken once.
+  __device__ __forceinline__ void row5(uint32_t lane, uint32_t line, uint8_t *row) const {
+    if (vblank & 2) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) row[lane + 32 * k] = 0;
+      return;
+    }
+    const uint32_t a = vp0 | vm0, b = vp1 | vm1, f = vpf, l = vbl;
+    uint32_t c[5];
+    if (ctrlpf & 4) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        c[k] = (((f | l) >> k) & 1u) ? colupf : ((a >> k) & 1u) ? colup0 : ((b >> k) & 1u) ? colup1 : colubk;
+    } else {
+      const uint32_t pl = (ctrlpf & 2) ? colup0 : colupf, pr = (ctrlpf & 2) ? colup1 : colupf;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const bool half = k >= 3 || (k == 2 && lane >= 16u);  // column lane + 32k >= 80
+        c[k] = ((a >> k) & 1u) ? colup0 : ((b >> k) & 1u) ? colup1 : ((f >> k) & 1u) ? (half ? pr : pl)
+             : ((l >> k) & 1u) ? colupf : colubk;
+      }
+    }
+    if (line == bar && lane < 8) c[0] = 0;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) row[lane + 32 * k] = (uint8_t)(c[k] & 0xFE);
+  }
   // Pixel of column lane + 32k on a frame-relative line (the lane's own column);
   // prepare() has run since the last write.
   __device__ __forceinline__ uint32_t pixel_k(uint32_t k, uint32_t lane, uint32_t line) const {
@@ -180,7 +208,9 @@ __device__ inline void render_frame_warp(RenderRegs &R, const uint32_t *recs, ui
         ++ri;
       }
       R.prepare(k < 5, lane);
-      for (; k < 5; ++k) row_buf[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
+      if (__all_sync(0xFFFFFFFFu, k == 0)) R.row5(lane, line, row_buf);
+      else
+        for (; k < 5; ++k) row_buf[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
     }
     __syncwarp();
     const uint32_t *src = reinterpret_cast<const uint32_t *>(row_buf);
