@@ -38,8 +38,8 @@ SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 # 16384 env-frames / 4096 env-steps), keyed by (workload config, form, envs
 # per warp).  They hold for the interpreter version captured there; a key
 # without an entry reports achieved = null.
-INTERP_WARP_INST_PER_ENV_FRAME = {(2, "batched", 32): 475210814 / 16384}
-INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 32): (1363968 + 65536) / 4096}
+INTERP_WARP_INST_PER_ENV_FRAME = {(2, "batched", 32): 476121189 / 16384}
+INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 32): (1278720 + 146432) / 4096}
 # Algorithmic bytes of the fused rasterise + preprocess kernel per env-step,
 # besides 4 bytes per logged TIA write: snapshots and record counts of the two
 # rendered frames (2 x 64 + 2 x 8), the three older stack planes read from the
@@ -48,7 +48,7 @@ INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 32): (1363968 + 65536) / 4096}
 FUSED_FIXED_BYTES_PER_ENV_STEP = 2 * 64 + 2 * 8 + 3 * 7056 + 4 * 7056 + 7056 + 1
 # DRAM bytes per env-step of the fused kernel from the capture summarised in
 # profiles/raster_preprocess_fused_sprite4096.md.
-FUSED_DRAM_BYTES_PER_ENV_STEP = {2: (107943424 + 94864896) / 4096}
+FUSED_DRAM_BYTES_PER_ENV_STEP = {2: (109457408 + 94802688) / 4096}
 
 
 def parse():
