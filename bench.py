@@ -36,10 +36,10 @@ SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 # profiles/interpreter_batched_sprite4096.md (smsp__inst_executed.sum and
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, divided by its
 # 16384 env-frames / 4096 env-steps), keyed by (workload config, form, envs
-# per warp).  They hold for the interpreter version captured there; a key
+# per warp, tia_warps).  They hold for the interpreter version captured there; a key
 # without an entry reports achieved = null.
-INTERP_WARP_INST_PER_ENV_FRAME = {(2, "batched", 32): 476121189 / 16384}
-INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 32): (1278720 + 146432) / 4096}
+INTERP_WARP_INST_PER_ENV_FRAME = {(2, "batched", 32, 1): 476121189 / 16384}
+INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 32, 1): (1278720 + 146432) / 4096}
 # Algorithmic bytes of the fused rasterise + preprocess kernel per env-step,
 # besides 4 bytes per logged TIA write: snapshots and record counts of the two
 # rendered frames (2 x 64 + 2 x 8), the three older stack planes read from the
@@ -68,6 +68,7 @@ def parse():
     p.add_argument("--envs-per-warp", type=int, default=0)
     p.add_argument("--envs-per-block", type=int, default=0)
     p.add_argument("--warps-per-frame", type=int, default=0)
+    p.add_argument("--tia-warps", type=int, default=0, choices=[0, 1, 2])
     return p.parse_args()
 
 
@@ -334,7 +335,8 @@ def main():
     env = AtariEnv([r.data for r in w.roms], [(r.score_addr, r.gameover_addr) for r in w.roms], w.env_rom,
                    luma=synth.luma_table(), env_key=env_key, frameskip=w.frameskip, sticky=w.sticky,
                    output_mode=w.output_mode, form=form, seed=w.seed, envs_per_warp=args.envs_per_warp,
-                   envs_per_block=args.envs_per_block, raster_warps_per_frame=args.warps_per_frame)
+                   envs_per_block=args.envs_per_block, raster_warps_per_frame=args.warps_per_frame,
+                   tia_warps=args.tia_warps)
     K, W = args.steps, args.warmup
     acts = torch.from_numpy(synth.actions(100 + rank, K + W, w.n_envs)).cuda()
     obs, rew, done = env.alloc_outputs()
@@ -426,7 +428,7 @@ def main():
     roof = None
     if interp_n:
         dur = interp_ms / interp_n / 1000.0
-        shape_key = (args.config, args.form, env.launch_shape()[0])
+        shape_key = (args.config, args.form, env.launch_shape()[0], env.launch_shape()[4])
         per = INTERP_WARP_INST_PER_ENV_FRAME.get(shape_key)
         peak = SM_COUNT * SMSP_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
         ach = per * w.n_envs * w.frameskip / dur / 1e9 if per else None
@@ -465,8 +467,8 @@ def main():
                        "n_envs": w.n_envs, "n_roms": len(w.roms), "frameskip": w.frameskip,
                        "output": "84x84x4 uint8 stack" if w.output_mode == 1 else "210x160 palette frame",
                        "form": args.form, "l2": "flushed (256 MB write) before each timed step",
-                       "launch_shape": dict(zip(["envs_per_warp", "envs_per_block", "warps_per_frame", "grid"],
-                                                env.launch_shape())),
+                       "launch_shape": dict(zip(["envs_per_warp", "envs_per_block", "warps_per_frame", "grid",
+                                                 "tia_warps"], env.launch_shape())),
                        "parallelism": f"replicas x{ws}"},
             "e2e": e2e, "roofline": roof, "roofline_fused": roof2, "kernels": kernels, "gpu_launches": gpu_launches,
             "m6502_inst_per_step": instr / K if K else None, "tia_log_records_per_step": logrec / K if K else None,

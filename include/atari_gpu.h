@@ -54,6 +54,7 @@ typedef void *atari_stream;           /* a cudaStream_t */
 #define ATARI_ST_FRAME_CAP 2u     /* a frame ran 400 lines without a VSYNC rise */
 #define ATARI_ST_LOG_OVERFLOW 4u  /* a rendered frame wrote more TIA registers than log_cap */
 #define ATARI_ST_BAD_ACTION 8u    /* an action >= 18 was taken as NOOP */
+#define ATARI_ST_STALL 16u        /* a bounded wait between an env's CPU and TIA warps ran out (tia_warps 2); the env halts */
 
 /* output modes */
 #define ATARI_OUT_PALETTE 0  /* d_obs = uint8 [n][210][160] palette values (COLU & 0xFE) of frame F */
@@ -85,6 +86,9 @@ typedef struct {
                              SIMT width for more independent instruction streams on small batches */
     int raster_warps_per_frame; /* batched form: warps rendering one frame, 1..4 (0 = autotune) */
     uint64_t seed;        /* Philox4x32-10 key for start states, resets and sticky draws */
+    int tia_warps;        /* batched form: 1 = each warp runs its envs' CPU and TIA; 2 = a TIA warp per
+                             CPU warp takes the TIA writes, logging and collisions off the CPU's
+                             path; 0 = autotune */
 } atari_config;
 
 /* Fill *cfg with the paper's defaults: F = 4, no sticky actions, 30 cached
@@ -223,9 +227,10 @@ ATARI_API int atari_env_profile_read(atari_env *env, double *ms, uint64_t *launc
 
 /* Launch shape in use (batched form: the autotuned or configured values;
  * plain form: 32 envs per warp, 128 per block, 1 warp per frame, and the
- * grid of the interpreter launch).  Host pointers; any may be NULL. */
+ * grid of the interpreter launch).  tia_warps: 2 when paired TIA warps run
+ * the envs' TIA side, else 1.  Host pointers; any may be NULL. */
 ATARI_API int atari_env_launch_shape(atari_env *env, int *envs_per_warp, int *envs_per_block,
-                                     int *raster_warps_per_frame, int *grid);
+                                     int *raster_warps_per_frame, int *grid, int *tia_warps);
 
 /* Number of envs, and the bytes of device memory the env holds. */
 ATARI_API int atari_env_info(atari_env *env, int *n_envs, size_t *device_bytes);

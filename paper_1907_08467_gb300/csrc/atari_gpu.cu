@@ -468,6 +468,7 @@ struct atari_env {
   int32_t *d_grp = nullptr;         // rom, start, count per work item (3 * n_groups) then perm (n)
   int *d_queue = nullptr;
   int n_groups = 0, lanes = 32, warps = 4, wpf = 4, grid = 0, rom_stage = 4096, max_blocks = 1;
+  bool split = false;   // paired CPU / TIA warps (k_interp_split)
   std::vector<int32_t> h_env_rom;
   std::vector<uint32_t> h_banks;
   cudaStream_t cap_stream = nullptr;
@@ -502,8 +503,9 @@ int validate(const atari_config &c) {
   if (c.log_cap < 256 || c.log_cap > (1 << 20)) return fail(ATARI_EINVAL, "log_cap must be in 256..2^20");
   if (c.sticky != 0 && c.sticky != 1) return fail(ATARI_EINVAL, "sticky must be 0 or 1");
   if (c.envs_per_block < 0 || c.envs_per_block > 128 || c.envs_per_warp < 0 || c.envs_per_warp > 32 ||
-      c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4)
-    return fail(ATARI_EINVAL, "envs_per_block must be 0..128, envs_per_warp 0..32, raster_warps_per_frame 0..4");
+      c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4 || c.tia_warps < 0 || c.tia_warps > 2)
+    return fail(ATARI_EINVAL, "envs_per_block must be 0..128, envs_per_warp 0..32, raster_warps_per_frame 0..4, "
+                              "tia_warps 0..2");
   return 0;
 }
 
@@ -514,7 +516,7 @@ namespace {
 
 // Envs grouped by cartridge into work items of E envs (ascending env index
 // within a cartridge); uploads rom/start/count per item and the permutation.
-int build_groups(atari_env *E, int lanes, int warps) {
+int build_groups(atari_env *E, int lanes, int warps, bool split) {
   const int per = lanes * warps;
   std::vector<int32_t> rom, start, count, perm;
   perm.reserve(E->n);
@@ -542,10 +544,16 @@ int build_groups(atari_env *E, int lanes, int warps) {
   E->n_groups = ng;
   E->lanes = lanes;
   E->warps = warps;
-  size_t smem = (size_t)E->rom_stage + 16 + 512 + (size_t)lanes * warps * ENV_SMEM;
+  E->split = split;
+  const size_t smem = (size_t)E->rom_stage + 16 + 512 + (size_t)lanes * warps * (ENV_SMEM + (split ? 4 * QSTRIDE : 0));
   int per_sm = 0;
-  CUDA_TRY(cudaFuncSetAttribute(k_interp_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched, warps * 32, smem));
+  if (split) {
+    CUDA_TRY(cudaFuncSetAttribute(k_interp_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_split, 2 * warps * 32, smem));
+  } else {
+    CUDA_TRY(cudaFuncSetAttribute(k_interp_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched, warps * 32, smem));
+  }
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device));
   E->max_blocks = std::max(1, per_sm) * sms;
@@ -593,8 +601,14 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
 }
 
 size_t interp_smem(const atari_env *E) {
-  return (size_t)E->rom_stage + 16 + 512 + (size_t)E->lanes * E->warps * ENV_SMEM;
+  return (size_t)E->rom_stage + 16 + 512 + (size_t)E->lanes * E->warps * (ENV_SMEM + (E->split ? 4 * QSTRIDE : 0));
 }
+// The batched interpreter in the env's current form and shape.
+void launch_interp(atari_env *E, const BatchArgs &a, int grid, cudaStream_t s) {
+  if (E->split) k_interp_split<<<grid, 2 * E->warps * 32, interp_smem(E), s>>>(a);
+  else k_interp_batched<<<grid, E->warps * 32, interp_smem(E), s>>>(a);
+}
+
 size_t fused_smem() { return 2 * 210 * 160 + 128 + 7056; }
 
 struct ProfScope;  // defined below
@@ -886,7 +900,7 @@ int launch_batched(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
   CUDA_TRY(cudaMemsetAsync(E->d_queue, 0, sizeof(int), s));
   {
     ProfScope p(E, ATARI_PROF_INTERP, s);
-    k_interp_batched<<<E->grid, E->warps * 32, interp_smem(E), s>>>(a);
+    launch_interp(E, a, E->grid, s);
   }
   CUDA_TRY(cudaGetLastError());
   if (c.output_mode == ATARI_OUT_STACK) {
@@ -950,8 +964,10 @@ int autotune(atari_env *E) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cand[][2] = {{32, 4}, {32, 2}, {32, 1}, {16, 4}, {16, 2}, {16, 1}, {8, 4}, {8, 2}, {8, 1},
-                         {4, 4}, {4, 2}, {4, 1}, {2, 4}, {2, 2}, {1, 4}};
+  // (envs per warp, CPU warps per block, paired TIA warps)
+  const int cand[][3] = {{32, 4, 0}, {32, 2, 0}, {32, 1, 0}, {16, 4, 0}, {16, 2, 0}, {16, 1, 0}, {8, 4, 0},
+                         {8, 2, 0},  {8, 1, 0},  {4, 4, 0},  {4, 2, 0},  {4, 1, 0},  {2, 4, 0},  {2, 2, 0},
+                         {1, 4, 0},  {32, 4, 1}, {32, 2, 1}, {32, 1, 1}, {16, 4, 1}, {16, 2, 1}};
   // shapes within 3 % of the fastest count as equal; the first of them in
   // candidate order (the widest warps) is taken, so the choice is stable
   // from run to run
@@ -961,14 +977,15 @@ int autotune(atari_env *E) {
   for (int ci = 0; ci < (int)(sizeof cand / sizeof cand[0]); ++ci) {
     const auto &c = cand[ci];
     if ((size_t)c[0] * c[1] > 4 * n && c[0] * c[1] > 32) continue;  // far more slots than envs
-    if (int rc = build_groups(E, c[0], c[1])) { cudaFree(st_bak); return rc; }
+    if ((E->cfg.tia_warps == 1 && c[2]) || (E->cfg.tia_warps == 2 && !c[2])) continue;
+    if (int rc = build_groups(E, c[0], c[1], c[2] != 0)) { cudaFree(st_bak); return rc; }
     BatchArgs a = batch_args(E, E->d_act, nullptr, nullptr);
     float t = 0;
     for (int rep = 0; rep < 2; ++rep) {
       CUDA_TRY(cudaMemcpy(E->d_state, st_bak, n * 256, cudaMemcpyDeviceToDevice));
       CUDA_TRY(cudaMemset(E->d_queue, 0, sizeof(int)));
       cudaEventRecord(e0);
-      k_interp_batched<<<E->grid, E->warps * 32, interp_smem(E)>>>(a);
+      launch_interp(E, a, E->grid, nullptr);
       cudaEventRecord(e1);
       CUDA_TRY(cudaEventSynchronize(e1));
       CUDA_TRY(cudaGetLastError());
@@ -978,10 +995,10 @@ int autotune(atari_env *E) {
   }
   float best = 1e30f;
   for (auto &p : timed) best = std::min(best, p.first);
-  int bl = 32, bw = 4;
+  int bl = 32, bw = 4, bs = E->cfg.tia_warps == 2 ? 1 : 0;
   for (auto &p : timed)
-    if (p.first <= 1.03f * best) { bl = cand[p.second][0]; bw = cand[p.second][1]; break; }
-  int rc = build_groups(E, bl, bw);
+    if (p.first <= 1.03f * best) { bl = cand[p.second][0]; bw = cand[p.second][1]; bs = cand[p.second][2]; break; }
+  int rc = build_groups(E, bl, bw, bs != 0);
   if (!rc && E->cfg.output_mode == ATARI_OUT_STACK) {
     if (!(rc = dalloc(&ring_bak, n * 4 * 7056, dummy)) && !(rc = dalloc(&head_bak, n, dummy))) {
       cudaMemcpy(ring_bak, E->d_ring, n * 4 * 7056, cudaMemcpyDeviceToDevice);
@@ -1047,9 +1064,9 @@ int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vect
   if (c.envs_per_block > 0 && c.envs_per_warp > 0) {
     int L = std::min(32, c.envs_per_warp), W = std::max(1, std::min(4, c.envs_per_block / L));
     E->wpf = c.raster_warps_per_frame > 0 ? c.raster_warps_per_frame : 4;
-    return build_groups(E, L, W);
+    return build_groups(E, L, W, c.tia_warps == 2);
   }
-  if (E->n == 0) return build_groups(E, 32, 4);
+  if (E->n == 0) return build_groups(E, 32, 4, c.tia_warps == 2);
   return autotune(E);
 }
 }  // namespace
@@ -1215,7 +1232,7 @@ int atari_env_profile_read(atari_env *E, double *ms, uint64_t *launches) {
 }
 
 int atari_env_launch_shape(atari_env *E, int *envs_per_warp, int *envs_per_block, int *raster_warps_per_frame,
-                           int *grid) {
+                           int *grid, int *tia_warps) {
   g_err.clear();
   if (!E) return fail(ATARI_EINVAL, "env is NULL");
   const bool b = E->cfg.form == ATARI_FORM_BATCHED;
@@ -1223,6 +1240,7 @@ int atari_env_launch_shape(atari_env *E, int *envs_per_warp, int *envs_per_block
   if (envs_per_block) *envs_per_block = b ? E->lanes * E->warps : 128;
   if (raster_warps_per_frame) *raster_warps_per_frame = b ? E->wpf : 1;
   if (grid) *grid = b ? E->grid : (E->n + 127) / 128;
+  if (tia_warps) *tia_warps = (b && E->split) ? 2 : 1;
   return 0;
 }
 
@@ -1449,7 +1467,7 @@ int serve_tick(atari_env *E, const ServeTick &t, cudaStream_t s) {
   a.n_groups = t.n_groups;
   CUDA_TRY(cudaMemsetAsync(t.d_queue, 0, sizeof(int), s));
   const int grid = std::max(1, std::min(t.n_groups, E->max_blocks));
-  k_interp_batched<<<grid, E->warps * 32, interp_smem(E), s>>>(a);
+  launch_interp(E, a, grid, s);
   CUDA_TRY(cudaGetLastError());
   k_raster_preprocess<<<t.n_active, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma,
                                                                    E->d_ring, E->d_head, E->d_done, t.d_obs,

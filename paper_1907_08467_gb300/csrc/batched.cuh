@@ -63,7 +63,10 @@ __device__ __forceinline__ void fast_reset_from_cache(uint8_t *st, const uint8_t
 }
 
 // Env slot i; o = where its action is read and its reward and done written.
-__device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i, int o, const BatchArgs &a,
+// Split form: logged-frame setup, frame records and the log count happen on
+// the TIA side, in queue order; the step ends once the TIA side has caught up.
+template <bool SPLIT>
+__device__ __forceinline__ void fast_step_env(FastConsoleT<SPLIT> &m, uint8_t *st, int i, int o, const BatchArgs &a,
                                               uint32_t rom, uint32_t score, uint32_t gameover) {
   const uint32_t *ew = reinterpret_cast<const uint32_t *>(st + S::EPISODE);
   uint32_t episode = ew[0], step_no = ew[1], env_key = ew[2], env_status = ew[3];
@@ -84,25 +87,35 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
     m.apply_action(act);
     const int slot = f - (F - 1);
     const bool logging = slot >= a.first_slot;
-    if (logging) {
-      m.snapshot(a.snap + ((size_t)i * 2 + slot) * 64);
-      m.set_log(a.log + ((size_t)i * 2 + slot) * a.log_cap, (uint32_t)a.log_cap,
-                a.bsnap ? a.bsnap + ((size_t)i * 2 + slot) * 3 * 64 : nullptr);
+    if constexpr (SPLIT) {
+      if (logging) m.push(EV_BEGIN_LOG | (uint32_t)slot);
+      m.run_frame();
+      if (logging) m.push(EV_END_LOG | (uint32_t)slot);
     } else {
-      m.set_log(nullptr, 0, nullptr);
-    }
-    const uint32_t lines = m.run_frame();
-    if (logging) {
-      m.finish_bands();
-      uint32_t *mt = a.meta + ((size_t)i * 2 + slot) * 2;
-      const uint32_t nrec = m.log_count();
-      mt[0] = nrec;
-      mt[1] = lines;
-      log_total += nrec;
+      if (logging) {
+        m.snapshot(a.snap + ((size_t)i * 2 + slot) * 64);
+        m.set_log(a.log + ((size_t)i * 2 + slot) * a.log_cap, (uint32_t)a.log_cap,
+                  a.bsnap ? a.bsnap + ((size_t)i * 2 + slot) * 3 * 64 : nullptr);
+      } else {
+        m.set_log(nullptr, 0, nullptr);
+      }
+      const uint32_t lines = m.run_frame();
+      if (logging) {
+        m.finish_bands();
+        uint32_t *mt = a.meta + ((size_t)i * 2 + slot) * 2;
+        const uint32_t nrec = m.log_count();
+        mt[0] = nrec;
+        mt[1] = lines;
+        log_total += nrec;
+      }
     }
     const uint32_t s = m.ram[score];
     reward += (int32_t)(int8_t)(uint8_t)(s - score_prev);
     score_prev = s;
+  }
+  if constexpr (SPLIT) {
+    m.push(EV_STEP_END);
+    m.wait_ack(m.nreq + 1);
   }
   env_status |= m.all_status();
   if (m.jam) env_status |= ST_ILLEGAL;
@@ -113,7 +126,7 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
   if (a.done_out) a.done_out[o] = (uint8_t)done;
   if (a.counters) {
     a.counters[2 * i] = m.instret;
-    a.counters[2 * i + 1] = log_total;
+    if constexpr (!SPLIT) a.counters[2 * i + 1] = log_total;
   }
   uint32_t *ewo = reinterpret_cast<uint32_t *>(st + S::EPISODE);
   ewo[1] = step_no + 1;
@@ -124,6 +137,60 @@ __device__ __forceinline__ void fast_step_env(FastConsole &m, uint8_t *st, int i
     m.store(st);
     st[S::LAST_ACTION] = (uint8_t)last;
     st[S::SCORE_PREV] = (uint8_t)score_prev;
+  }
+}
+
+// TIA side of the split form for env slot i: applies the CPU side's events in
+// order until the end of the step.  Every wait is bounded; running out sets
+// ST_STALL and ends the loop.
+__device__ void tia_worker(IoCtx c, const uint32_t *q, int i, const BatchArgs &a) {
+  volatile uint32_t *vw = reinterpret_cast<volatile uint32_t *>(c.w());
+  const volatile uint32_t *vq = reinterpret_cast<const volatile uint32_t *>(q);
+  uint32_t head = 0, ack = 0, lines = 0, log_total = 0, spins = 0;
+  for (;;) {
+    if (head == vw[IO_QTAIL]) {
+      if (++spins > SPIN_LIMIT) {
+        c.Sset(IO_STATUS, c.G(IO_STATUS) | ST_STALL);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    spins = 0;
+    __threadfence_block();
+    const uint32_t ev = vq[head & (QLEN - 1)];
+    vw[IO_QHEAD] = ++head;
+    const uint32_t kind = ev >> 30;
+    if (kind == 0) {
+      fc_tia_write(c, (ev >> 8) & 0x3F, ev & 0xFF, (ev >> 14) & 0xFFFF, false);
+    } else if (kind == 1) {
+      lines = ev & 0x3FFF;
+      fc_frame_end(c, (ev >> 14) & 0xFFFF, lines);
+    } else {
+      const uint32_t sub = (ev >> 28) & 3, slot = ev & 1;
+      if (sub == 0) {
+        fc_snapshot(c, a.snap + ((size_t)i * 2 + slot) * 64, 0);
+        fc_set_log(c, a.log + ((size_t)i * 2 + slot) * a.log_cap, (uint32_t)a.log_cap,
+                   a.bsnap ? a.bsnap + ((size_t)i * 2 + slot) * 3 * 64 : nullptr);
+      } else if (sub == 1) {
+        if (c.G(IO_BANDN) < 4) fc_band_snap(c, ~0u);
+        const uint32_t nrec = c.G(IO_LOGN);
+        uint32_t *mt = a.meta + ((size_t)i * 2 + slot) * 2;
+        mt[0] = nrec;
+        mt[1] = lines;
+        log_total += nrec;
+        fc_set_log(c, nullptr, 0, nullptr);
+      } else if (sub == 2) {
+        fc_cx_eval(c, 3u * (ev & 0xFFFFu));
+        __threadfence_block();
+        vw[IO_ACK] = ++ack;
+      } else {
+        if (a.counters) a.counters[2 * i + 1] = log_total;
+        __threadfence_block();
+        vw[IO_ACK] = ++ack;
+        break;
+      }
+    }
   }
 }
 
@@ -175,6 +242,70 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
         m.load(st);
         fast_step_env(m, st, i, o, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
       }
+    }
+  }
+}
+
+// Split form: blockDim = 2 W warps; warps [0, W) run the CPUs of the work
+// item's envs, warp W + w the TIA side of CPU warp w's envs (lane for lane).
+// Shared memory: cartridge stage, decoder table, per-env RAM, I/O words, TIA
+// file, then the per-env event queues.
+__global__ void __launch_bounds__(256, 1) k_interp_split(BatchArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t *rom8 = smem;
+  uint8_t *dec_op = smem + (size_t)a.rom_stage + 16;
+  uint32_t *ram = reinterpret_cast<uint32_t *>(dec_op + 512);
+  uint32_t *iow = ram + RAM_STRIDE * a.E;
+  uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_STRIDE * a.E);
+  uint32_t *qs = reinterpret_cast<uint32_t *>(tia + TIA_STRIDE * a.E);
+  __shared__ int s_group;
+  for (int t = threadIdx.x; t < 512; t += blockDim.x) dec_op[t] = a.dec_op[t];
+  int cur_rom = -1;
+  const int W = a.E / a.lanes;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool cpu = warp < W;
+  const int cw = cpu ? warp : warp - W;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_group = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int g = s_group;
+    if (g >= a.n_groups) break;
+    const int rom = a.grp_rom[g];
+    if (rom != cur_rom) {
+      const uint32_t banks = a.info[rom] >> 24;
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.romb + (size_t)rom * 16384);
+      uint4 *dst = reinterpret_cast<uint4 *>(rom8);
+      for (uint32_t q = threadIdx.x; q < banks * 256u; q += blockDim.x) dst[q] = src[q];
+      if (threadIdx.x == 0) dst[banks * 256u] = make_uint4(0, 0, 0, 0);
+      cur_rom = rom;
+      __syncthreads();
+    }
+    const int jj = cw * a.lanes + lane;
+    const bool runs = lane < a.lanes && jj < a.grp_count[g];
+    const uint32_t wmask = __ballot_sync(0xFFFFFFFFu, runs);
+    const int p = a.grp_start[g] + jj;
+    const int i = runs ? a.perm[p] : 0;
+    const int o = runs ? (a.opos ? a.opos[p] : i) : 0;
+    uint8_t *st = a.state + (size_t)i * 256;
+    const uint32_t inf = a.info[rom];
+    const IoCtx io{tia + TIA_STRIDE * jj, iow + IO_STRIDE * jj};
+    uint32_t *q = qs + QSTRIDE * jj;
+    FastConsoleT<true> m;
+    if (cpu && runs) {
+      m.rom8 = rom8;
+      m.dec_op = dec_op;
+      m.ram = ram + RAM_STRIDE * jj;
+      m.io = io;
+      m.q = q;
+      m.scheme = inf & 0xFF;
+      m.wmask = wmask;
+      m.load(st);
+    }
+    __syncthreads();  // the envs' state is in shared memory before the TIA side starts
+    if (runs) {
+      if (cpu) fast_step_env<true>(m, st, i, o, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
+      else tia_worker(io, q, i, a);
     }
   }
 }

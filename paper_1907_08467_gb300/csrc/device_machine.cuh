@@ -36,7 +36,7 @@ constexpr int EPISODE = 0x60, STEP = 0x64, ENV_KEY = 0x68, STATUS = 0x6C, LAST_A
 constexpr int MACHINE_END = 0x60;  // bytes [0, 0x60) and [0x80, 0x100) are machine state
 }  // namespace S
 
-constexpr uint32_t ST_ILLEGAL = 1u, ST_FRAME_CAP = 2u, ST_LOG_OVERFLOW = 4u, ST_BAD_ACTION = 8u;
+constexpr uint32_t ST_ILLEGAL = 1u, ST_FRAME_CAP = 2u, ST_LOG_OVERFLOW = 4u, ST_BAD_ACTION = 8u, ST_STALL = 16u;
 constexpr uint64_t NO_LINE = ~0ull;
 constexpr int WINDOW_Y0 = 31, FRAME_H = 210, FRAME_W = 160, CAP_LINES = 400;
 

@@ -35,7 +35,8 @@ enum IoWord : uint32_t {
   IO_JOY, IO_FIRE, IO_LATCH, IO_LOGLO, IO_LOGHI, IO_LOGN, IO_LOGCAP, IO_STATUS,
   IO_BANDN,      // next quarter-frame band whose start snapshot is due (1..3), 4: none
   IO_BSLO, IO_BSHI,  // where this frame's band snapshots go (3 x 64 bytes)
-  IO_PAD, IO_WORDS
+  IO_QHEAD, IO_QTAIL, IO_ACK,  // split form: TIA event queue cursors and the TIA side's acknowledgements
+  IO_WORDS
 };
 constexpr uint32_t IO_WSYNC = 1u, IO_VSYNC_RISE = 2u;
 
@@ -150,18 +151,8 @@ __device__ __forceinline__ uint32_t fc_hm_move(uint32_t pos, uint32_t hm) {
 }
 
 // Read a TIA or RIOT address (13-bit, neither RAM nor cartridge) at cycle t.
-__device__ __noinline__ uint32_t fc_io_read(IoCtx c, uint32_t a, uint32_t t) {
-  if (!(a & 0x80)) {
-    const uint32_t reg = a & 0x0F;
-    if (reg < 8) {
-      fc_cx_eval(c, 3u * t);
-      const uint32_t cx = c.G(IO_CX);
-      return (((cx >> (2 * reg + 1)) & 1u) << 7) | (((cx >> (2 * reg)) & 1u) << 6);
-    }
-    if (reg == 0x0C) return (c.G(IO_FIRE) || c.G(IO_LATCH)) ? 0x00u : 0x80u;
-    if (reg == 0x0D) return 0x80u;
-    return 0;
-  }
+// Read a RIOT address (ports, timer) at absolute CPU cycle `now`.
+__device__ __forceinline__ uint32_t fc_riot_read(IoCtx c, uint32_t a, uint64_t now) {
   const uint32_t ports = c.G(IO_PORTS);
   if (!(a & 4)) {
     const uint32_t sh = 8 * (a & 2);             // SWCHA/SWACNT in bytes 0/1, SWCHB/SWBCNT in 2/3
@@ -170,13 +161,30 @@ __device__ __noinline__ uint32_t fc_io_read(IoCtx c, uint32_t a, uint32_t t) {
     const uint32_t pins = (a & 2) ? 0x0Bu : c.G(IO_JOY);
     return ((out & ddr) | (pins & ~ddr)) & 0xFF;
   }
-  const uint64_t now = 76ull * c.G64(IO_L0LO) + t;
   const uint64_t n = now - (c.G64(IO_TCWLO) + 1);
   const uint32_t tv = c.G(IO_TV), sh = c.G(IO_TSH);
   const uint64_t span = (uint64_t)(tv + 1) << sh;
   if (a & 1) return n >= span ? 0x80u : 0u;
   if (n < span) return tv - (uint32_t)(n >> sh);
   return (uint32_t)(0xFFull - (n - span)) & 0xFF;
+}
+// Collision-latch byte of TIA read register reg (0..7) from the CX word.
+__device__ __forceinline__ uint32_t fc_cx_byte(uint32_t cx, uint32_t reg) {
+  return (((cx >> (2 * reg + 1)) & 1u) << 7) | (((cx >> (2 * reg)) & 1u) << 6);
+}
+// Read a TIA or RIOT address (13-bit, neither RAM nor cartridge) at cycle t.
+__device__ __noinline__ uint32_t fc_io_read(IoCtx c, uint32_t a, uint32_t t) {
+  if (!(a & 0x80)) {
+    const uint32_t reg = a & 0x0F;
+    if (reg < 8) {
+      fc_cx_eval(c, 3u * t);
+      return fc_cx_byte(c.G(IO_CX), reg);
+    }
+    if (reg == 0x0C) return (c.G(IO_FIRE) || c.G(IO_LATCH)) ? 0x00u : 0x80u;
+    if (reg == 0x0D) return 0x80u;
+    return 0;
+  }
+  return fc_riot_read(c, a, 76ull * c.G64(IO_L0LO) + t);
 }
 
 // 64-byte render snapshot: TIA file (canonical bytes 0x20..0x44), HMOVE bar
@@ -217,6 +225,18 @@ __device__ __noinline__ void fc_band_snap(IoCtx c, uint32_t eff) {
   c.Sset(IO_BANDN, bn);
 }
 
+// Log the frame's TIA writes to p (cap records; p null: no log); bands:
+// where the three quarter-frame start snapshots go, or null for none.
+__device__ __forceinline__ void fc_set_log(IoCtx c, uint32_t *p, uint32_t cap, uint8_t *bands) {
+  c.Sset(IO_LOGLO, (uint32_t)(uint64_t)p);
+  c.Sset(IO_LOGHI, (uint32_t)((uint64_t)p >> 32));
+  c.Sset(IO_LOGN, 0);
+  c.Sset(IO_LOGCAP, cap);
+  c.Sset(IO_BANDN, bands ? 1u : 4u);
+  c.Sset(IO_BSLO, (uint32_t)(uint64_t)bands);
+  c.Sset(IO_BSHI, (uint32_t)((uint64_t)bands >> 32));
+}
+
 // Append one TIA write record (effect clock, register, value) to the log of
 // a rendered frame.
 __device__ __forceinline__ void fc_log(IoCtx c, uint32_t eff, uint32_t reg, uint32_t v) {
@@ -235,21 +255,22 @@ __device__ __forceinline__ void fc_log(IoCtx c, uint32_t eff, uint32_t reg, uint
 // no collision or timing effect (COLUP0, COLUP1, COLUPF, COLUBK, HMP0..HMBL).
 constexpr uint64_t FAST_TIA_REGS = (0xFull << 0x06) | (0x1Full << 0x20);
 
-// Write a TIA or RIOT address at cycle t; returns IO_WSYNC / IO_VSYNC_RISE.
-__device__ __noinline__ uint32_t fc_io_write(IoCtx c, uint32_t a, uint32_t v, uint32_t t) {
-  if (a & 0x80) {  // RIOT
-    if (!(a & 4)) {
-      const uint32_t sh = 8 * (a & 3);
-      c.Sset(IO_PORTS, (c.G(IO_PORTS) & ~(0xFFu << sh)) | (v & 0xFF) << sh);
-    } else if (a & 0x10) {
-      const uint32_t sel = a & 3;
-      c.Sset(IO_TV, v & 0xFF);
-      c.Sset(IO_TSH, sel == 0 ? 0 : sel == 1 ? 3 : sel == 2 ? 6 : 10);
-      c.S64(IO_TCWLO, 76ull * c.G64(IO_L0LO) + t);
-    }
-    return 0;
+// Write a RIOT address at absolute CPU cycle `now`.
+__device__ __forceinline__ void fc_riot_write(IoCtx c, uint32_t a, uint32_t v, uint64_t now) {
+  if (!(a & 4)) {
+    const uint32_t sh = 8 * (a & 3);
+    c.Sset(IO_PORTS, (c.G(IO_PORTS) & ~(0xFFu << sh)) | (v & 0xFF) << sh);
+  } else if (a & 0x10) {
+    const uint32_t sel = a & 3;
+    c.Sset(IO_TV, v & 0xFF);
+    c.Sset(IO_TSH, sel == 0 ? 0 : sel == 1 ? 3 : sel == 2 ? 6 : 10);
+    c.S64(IO_TCWLO, now);
   }
-  const uint32_t reg = a & 0x3F;
+}
+// The TIA part of a write (register reg at cycle t): collisions up to the
+// write, log record, register update.  cpu_latch: this thread also keeps the
+// fire-button latch (the split form keeps it on the CPU side).
+__device__ __forceinline__ uint32_t fc_tia_write(IoCtx c, uint32_t reg, uint32_t v, uint32_t t, bool cpu_latch) {
   const uint32_t eff = 3u * (t + 1u);
   if ((COLL_REGS >> reg) & 1ull) fc_cx_eval(c, eff);
   if ((LOG_REGS >> reg) & 1ull) fc_log(c, eff, reg, v);
@@ -261,8 +282,10 @@ __device__ __noinline__ uint32_t fc_io_write(IoCtx c, uint32_t a, uint32_t v, ui
       break;
     case 0x01:
       c.Tset(T_VBLANK, v);
-      if (!(v & 0x40)) c.Sset(IO_LATCH, 0);
-      else if (c.G(IO_FIRE)) c.Sset(IO_LATCH, 1);
+      if (cpu_latch) {
+        if (!(v & 0x40)) c.Sset(IO_LATCH, 0);
+        else if (c.G(IO_FIRE)) c.Sset(IO_LATCH, 1);
+      }
       break;
     case 0x02: flags |= IO_WSYNC; break;
     case 0x04: case 0x05: case 0x06: case 0x07: case 0x08: case 0x09: case 0x0A: case 0x0B: case 0x0C:
@@ -308,6 +331,14 @@ __device__ __noinline__ uint32_t fc_io_write(IoCtx c, uint32_t a, uint32_t v, ui
   }
   return flags;
 }
+// Write a TIA or RIOT address at cycle t; returns IO_WSYNC / IO_VSYNC_RISE.
+__device__ __noinline__ uint32_t fc_io_write(IoCtx c, uint32_t a, uint32_t v, uint32_t t) {
+  if (a & 0x80) {
+    fc_riot_write(c, a, v, 76ull * c.G64(IO_L0LO) + t);
+    return 0;
+  }
+  return fc_tia_write(c, a & 0x3F, v, t, true);
+}
 
 // End of a frame: collisions up to the current cycle, then rebase to the next frame.
 __device__ __noinline__ void fc_frame_end(IoCtx c, uint32_t kf, uint32_t next_rel) {
@@ -316,11 +347,33 @@ __device__ __noinline__ void fc_frame_end(IoCtx c, uint32_t kf, uint32_t next_re
   c.Sset(IO_CEVAL, c.G(IO_CEVAL) - 228u * next_rel);
 }
 
-// ---------------------------------------------------------------- the console
-struct FastConsole;
-__device__ __forceinline__ void fc_exec_general(FastConsole *self);
+// ---------------------------------------------------------------- split form
+// In the split form a block's warps come in pairs: a CPU warp runs the 6507
+// and RIOT and pushes every TIA write into a per-env queue in shared memory;
+// the paired TIA warp (same lane, same env) applies the writes, logs them and
+// evaluates collisions.  The CPU keeps its own copies of VSYNC, VBLANK, the
+// fire latch and the frame base line; it waits for the TIA side only when it
+// reads a collision register and at the end of the step.  Events (32 bits):
+//   write       0b00 | cycle:16 | register:6 | value:8
+//   frame end   0b01 | cycle of the end:16 | lines to the next frame:14
+//   control     0b10 | kind:2 | argument   (begin/end of a logged frame,
+//               collision sync up to a cycle, end of the step)
+constexpr uint32_t QLEN = 32;             // queue entries per env (a power of two)
+constexpr uint32_t QSTRIDE = QLEN + 1;    // shared-memory words per env queue (odd)
+constexpr uint32_t EV_WRITE = 0u, EV_FRAME_END = 1u << 30, EV_CTRL = 2u << 30;
+constexpr uint32_t EV_BEGIN_LOG = EV_CTRL, EV_END_LOG = EV_CTRL | 1u << 28, EV_SYNC = EV_CTRL | 2u << 28,
+                   EV_STEP_END = EV_CTRL | 3u << 28;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;  // polls of a queue cursor before the env is declared stalled
+// registers whose writes reach the TIA side (WSYNC, RSYNC, audio and unused
+// addresses change nothing there)
+constexpr uint64_t SPLIT_PUSH_REGS = LOG_REGS | COLL_REGS | 1ull | (1ull << 0x2C);
 
-struct FastConsole {
+// ---------------------------------------------------------------- the console
+template <bool SPLIT> struct FastConsoleT;
+template <bool SPLIT> __device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT> *self);
+
+template <bool SPLIT>
+struct FastConsoleT {
   const uint8_t *rom8;     // staged cartridge bytes (banks of 4096, then 16 bytes of padding)
   const uint8_t *dec_op;   // general decoder: opcode -> operation, then mode/cycles/penalty
   uint32_t *ram;           // this env's RAM block, one word per byte
@@ -332,6 +385,10 @@ struct FastConsole {
   uint32_t vs_kf;          // cycle of a VSYNC rise in this frame, ~0 if none
   uint32_t status, instret, frame_no;
   uint32_t wmask;          // lanes of this warp running envs (lockstep issue)
+  // split form: this env's TIA event queue and the CPU side's copies
+  uint32_t *q;
+  uint32_t qtail, nreq, vsync_c, vblank_c, broken;
+  uint64_t l0c;
 
   __device__ __forceinline__ uint32_t P() const {
     return (fn & 0x80) | fv | 0x20 | fdi | ((fz & 0xFF) ? 0u : 2u) | fc;
@@ -380,6 +437,13 @@ struct FastConsole {
       for (int b = 0; b < 16; ++b) ram[q * 16 + b] = (ws[b >> 2] >> (8 * (b & 3))) & 0xFF;
     }
     status = 0; instret = 0; pend = 0; vs_kf = ~0u;
+    if constexpr (SPLIT) {
+      vsync_c = io.T(T_VSYNC);
+      vblank_c = io.T(T_VBLANK);
+      l0c = L0;
+      qtail = nreq = broken = 0;
+      io.Sset(IO_QHEAD, 0); io.Sset(IO_QTAIL, 0); io.Sset(IO_ACK, 0);
+    }
   }
   __device__ void store(uint8_t *s) const {
     uint32_t *w = reinterpret_cast<uint32_t *>(s);
@@ -419,17 +483,7 @@ struct FastConsole {
     }
   }
   __device__ void snapshot(uint8_t *o) const { fc_snapshot(io, o, 0); }
-  // Log the frame's TIA writes to p (cap records); bands: where the three
-  // quarter-frame start snapshots go, or null for none.
-  __device__ void set_log(uint32_t *p, uint32_t cap, uint8_t *bands) {
-    io.Sset(IO_LOGLO, (uint32_t)(uint64_t)p);
-    io.Sset(IO_LOGHI, (uint32_t)((uint64_t)p >> 32));
-    io.Sset(IO_LOGN, 0);
-    io.Sset(IO_LOGCAP, cap);
-    io.Sset(IO_BANDN, bands ? 1u : 4u);
-    io.Sset(IO_BSLO, (uint32_t)(uint64_t)bands);
-    io.Sset(IO_BSHI, (uint32_t)((uint64_t)bands >> 32));
-  }
+  __device__ void set_log(uint32_t *p, uint32_t cap, uint8_t *bands) { fc_set_log(io, p, cap, bands); }
   // Band starts the frame never reached take its final state.
   __device__ void finish_bands() {
     if (io.G(IO_BANDN) < 4) fc_band_snap(io, ~0u);
@@ -454,7 +508,8 @@ struct FastConsole {
                               ((d & 1) ? 0x10u : 0u)));
     const uint32_t fire = (a == 1 || a >= 10) ? 1u : 0u;
     io.Sset(IO_FIRE, fire);
-    if (fire && (io.T(T_VBLANK) & 0x40)) io.Sset(IO_LATCH, 1);
+    const uint32_t vb = SPLIT ? vblank_c : io.T(T_VBLANK);
+    if (fire && (vb & 0x40)) io.Sset(IO_LATCH, 1);
   }
 
   // Cartridge bytes i .. i+3 of the stage, byte i lowest (i + 3 may run into
@@ -473,18 +528,97 @@ struct FastConsole {
   __device__ __forceinline__ void note_vsync(uint32_t t) {
     if (vs_kf == ~0u) vs_kf = t;
   }
-  // zero-page access: RAM for $80-$FF, TIA below
-  __device__ __forceinline__ uint32_t rdz(uint32_t z, uint32_t t) {
-    return (z & 0x80) ? ram[z & 0x7F] : fc_io_read(io, z, t);
+  // ---- split form: the queue to the TIA side ----
+  __device__ __forceinline__ volatile uint32_t *vio(uint32_t i) const {
+    return reinterpret_cast<volatile uint32_t *>(io.w() + i);
   }
-  __device__ __forceinline__ void wrz(uint32_t z, uint32_t v, uint32_t t) {
-    if (z & 0x80) {
-      ram[z & 0x7F] = v & 0xFF;
+  __device__ __forceinline__ void stall() {
+    broken = 1;
+    status |= ST_STALL;
+    jam = 1;
+  }
+  // Append an event (waits, bounded, while the queue is full).
+  __device__ __forceinline__ void push(uint32_t ev) {
+    if (broken) return;
+    uint32_t spins = 0;
+    while (qtail - *vio(IO_QHEAD) >= QLEN) {
+      if (++spins > SPIN_LIMIT) { stall(); return; }
+      __nanosleep(32);
+    }
+    reinterpret_cast<volatile uint32_t *>(q)[qtail & (QLEN - 1)] = ev;
+    __threadfence_block();
+    ++qtail;
+    *vio(IO_QTAIL) = qtail;
+  }
+  // Wait (bounded) until the TIA side has acknowledged n events.
+  __device__ __forceinline__ void wait_ack(uint32_t n) {
+    if (broken) return;
+    uint32_t spins = 0;
+    while ((int32_t)(*vio(IO_ACK) - n) < 0) {
+      if (++spins > SPIN_LIMIT) { stall(); return; }
+      __nanosleep(32);
+    }
+    __threadfence_block();
+  }
+  // TIA write in the split form: WSYNC, the VSYNC rise and the VBLANK latch
+  // effects here, the register itself on the TIA side.
+  __device__ __forceinline__ void tia_out(uint32_t reg, uint32_t v, uint32_t t) {
+    if (reg == 0x02) { pend |= IO_WSYNC; return; }
+    if (reg == 0x00) {
+      if (!(vsync_c & 2) && (v & 2)) { pend |= IO_VSYNC_RISE; note_vsync(t); }
+      vsync_c = v;
+    } else if (reg == 0x01) {
+      vblank_c = v;
+      if (!(v & 0x40)) io.Sset(IO_LATCH, 0);
+      else if (io.G(IO_FIRE)) io.Sset(IO_LATCH, 1);
+    }
+    if ((SPLIT_PUSH_REGS >> reg) & 1ull) push(EV_WRITE | t << 14 | reg << 8 | v);
+  }
+  // Read / write a TIA or RIOT address at cycle t.
+  __device__ __forceinline__ uint32_t io_read(uint32_t a, uint32_t t) {
+    if constexpr (!SPLIT) {
+      return fc_io_read(io, a, t);
     } else {
-      const uint32_t f = fc_io_write(io, z, v & 0xFF, t);
+      if (!(a & 0x80)) {
+        const uint32_t reg = a & 0x0F;
+        if (reg < 8) {  // collision latches: the TIA side evaluates them up to this cycle first
+          push(EV_SYNC | (t & 0xFFFFu));
+          wait_ack(++nreq);
+          return fc_cx_byte(*vio(IO_CX), reg);
+        }
+        if (reg == 0x0C) return (io.G(IO_FIRE) || io.G(IO_LATCH)) ? 0x00u : 0x80u;
+        if (reg == 0x0D) return 0x80u;
+        return 0;
+      }
+      return fc_riot_read(io, a, 76ull * l0c + t);
+    }
+  }
+  __device__ __forceinline__ void io_write(uint32_t a, uint32_t v, uint32_t t) {
+    if constexpr (!SPLIT) {
+      const uint32_t f = fc_io_write(io, a, v, t);
       pend |= f;
       if (f & IO_VSYNC_RISE) note_vsync(t);
+    } else {
+      if (a & 0x80) fc_riot_write(io, a, v, 76ull * l0c + t);
+      else tia_out(a & 0x3F, v, t);
     }
+  }
+  __device__ __forceinline__ void frame_end_out(uint32_t next_rel) {
+    if constexpr (!SPLIT) {
+      fc_frame_end(io, kf, next_rel);
+    } else {
+      push(EV_FRAME_END | kf << 14 | next_rel);
+      l0c += next_rel;
+    }
+  }
+
+  // zero-page access: RAM for $80-$FF, TIA below
+  __device__ __forceinline__ uint32_t rdz(uint32_t z, uint32_t t) {
+    return (z & 0x80) ? ram[z & 0x7F] : io_read(z, t);
+  }
+  __device__ __forceinline__ void wrz(uint32_t z, uint32_t v, uint32_t t) {
+    if (z & 0x80) ram[z & 0x7F] = v & 0xFF;
+    else io_write(z, v & 0xFF, t);
   }
   __device__ __forceinline__ uint32_t rd(uint32_t addr, uint32_t t) {
     const uint32_t a = addr & 0x1FFF;
@@ -494,15 +628,13 @@ struct FastConsole {
       if (scheme) hotspot(off);
       return rom8[bank * 4096u + off];
     }
-    return fc_io_read(io, a, t);
+    return io_read(a, t);
   }
   __device__ __forceinline__ void wr(uint32_t addr, uint32_t v, uint32_t t) {
     const uint32_t a = addr & 0x1FFF;
     if ((a & 0x1280) == 0x0080) { ram[a & 0x7F] = v & 0xFF; return; }
     if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
-    const uint32_t f = fc_io_write(io, a, v & 0xFF, t);
-    pend |= f;
-    if (f & IO_VSYNC_RISE) note_vsync(t);
+    io_write(a, v & 0xFF, t);
   }
 
   // Store instructions write through here (one inlined copy): RAM, cartridge
@@ -514,6 +646,10 @@ struct FastConsole {
     if (a & 0x1000) { if (scheme) hotspot(a & 0xFFF); return; }
     if (!(a & 0x80)) {
       const uint32_t reg = a & 0x3F;
+      if constexpr (SPLIT) {
+        tia_out(reg, v & 0xFF, t);
+        return;
+      }
       if (reg == 0x02) { pend |= IO_WSYNC; return; }
       if ((FAST_TIA_REGS >> reg) & 1ull) {
         fc_log(io, 3u * (t + 1u), reg, v & 0xFF);
@@ -521,9 +657,7 @@ struct FastConsole {
         return;
       }
     }
-    const uint32_t f = fc_io_write(io, a, v & 0xFF, t);
-    pend |= f;
-    if (f & IO_VSYNC_RISE) note_vsync(t);
+    io_write(a, v & 0xFF, t);
   }
 
   // ---- ALU ----
@@ -927,31 +1061,39 @@ struct FastConsole {
           next_rel = kf / 76u;
           active = false;
         } else {
-          if (!exec(w)) fc_exec_general(this);
+          if (!exec(w)) fc_exec_general<SPLIT>(this);
           if (jam) { next_rel = kf / 76u; active = false; }
           else if (vs_kf != ~0u) { next_rel = vs_kf / 76u; active = false; }
           else if (kf >= 76u * CAP_LINES) { status |= ST_FRAME_CAP; next_rel = kf / 76u; active = false; }
         }
       }
     }
-    fc_frame_end(io, kf, next_rel);
+    frame_end_out(next_rel);
     kf -= 76u * next_rel;
     frame_no++;
     return next_rel;
   }
 };
 
+using FastConsole = FastConsoleT<false>;
+
 // Out-of-line general instruction on a copy of the console.  Only the CPU
 // and timing state comes back: the caller's pointers into shared memory are
 // never reloaded from the copy, so they keep their shared address space.
-__device__ __noinline__ void fc_exec_general_impl(FastConsole *c) { c->exec_general(); }
-__device__ __forceinline__ void fc_exec_general(FastConsole *self) {
-  FastConsole tmp = *self;
-  fc_exec_general_impl(&tmp);
+template <bool SPLIT>
+__device__ __noinline__ void fc_exec_general_impl(FastConsoleT<SPLIT> *c) { c->exec_general(); }
+template <bool SPLIT>
+__device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT> *self) {
+  FastConsoleT<SPLIT> tmp = *self;
+  fc_exec_general_impl<SPLIT>(&tmp);
   self->A = tmp.A; self->X = tmp.X; self->Y = tmp.Y; self->SP = tmp.SP; self->PC = tmp.PC;
   self->fc = tmp.fc; self->fv = tmp.fv; self->fn = tmp.fn; self->fz = tmp.fz; self->fdi = tmp.fdi;
   self->bank = tmp.bank; self->jam = tmp.jam; self->kf = tmp.kf; self->pend = tmp.pend; self->vs_kf = tmp.vs_kf;
   self->status = tmp.status; self->instret = tmp.instret; self->frame_no = tmp.frame_no;
+  if constexpr (SPLIT) {
+    self->qtail = tmp.qtail; self->nreq = tmp.nreq; self->vsync_c = tmp.vsync_c; self->vblank_c = tmp.vblank_c;
+    self->broken = tmp.broken; self->l0c = tmp.l0c;
+  }
 }
 
 }  // namespace atari

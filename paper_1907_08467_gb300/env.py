@@ -16,7 +16,7 @@ from . import build as _build
 
 OUT_PALETTE, OUT_STACK = 0, 1
 FORM_PLAIN, FORM_BATCHED = 0, 1
-ST_ILLEGAL, ST_FRAME_CAP, ST_LOG_OVERFLOW, ST_BAD_ACTION = 1, 2, 4, 8
+ST_ILLEGAL, ST_FRAME_CAP, ST_LOG_OVERFLOW, ST_BAD_ACTION, ST_STALL = 1, 2, 4, 8, 16
 STATE_BYTES = 256
 
 _lock = threading.Lock()
@@ -27,7 +27,8 @@ class _Config(C.Structure):
     _fields_ = [("frameskip", C.c_int), ("sticky", C.c_int), ("n_cache", C.c_int),
                 ("startup_frames", C.c_int), ("max_noops", C.c_int), ("output_mode", C.c_int),
                 ("form", C.c_int), ("log_cap", C.c_int), ("envs_per_block", C.c_int),
-                ("envs_per_warp", C.c_int), ("raster_warps_per_frame", C.c_int), ("seed", C.c_uint64)]
+                ("envs_per_warp", C.c_int), ("raster_warps_per_frame", C.c_int), ("seed", C.c_uint64),
+                ("tia_warps", C.c_int)]
 
 
 class _Meta(C.Structure):
@@ -74,7 +75,7 @@ def load_library(path: str | None = None):
         L.atari_last_error.restype = C.c_char_p
         L.atari_env_profile.argtypes = [P, C.c_int]
         L.atari_env_profile_read.argtypes = [P, P, P]
-        L.atari_env_launch_shape.argtypes = [P, P, P, P, P]
+        L.atari_env_launch_shape.argtypes = [P, P, P, P, P, P]
         L.atari_step_noalloc.argtypes = [P, C.c_size_t, _Meta, P, P, C.c_int, P, P, P, P, C.c_int, C.c_int,
                                          C.c_int, C.c_uint64, P]
         L.atari_step_noalloc.restype = C.c_int
@@ -104,9 +105,9 @@ def _check(rc: int):
 
 def make_config(frameskip=4, sticky=False, n_cache=30, startup_frames=64, max_noops=30,
                 output_mode=OUT_STACK, form=FORM_PLAIN, log_cap=4096, envs_per_block=0, envs_per_warp=0,
-                raster_warps_per_frame=0, seed=1) -> _Config:
+                raster_warps_per_frame=0, seed=1, tia_warps=0) -> _Config:
     return _Config(frameskip, int(sticky), n_cache, startup_frames, max_noops, output_mode, form,
-                   log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed)
+                   log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed, tia_warps)
 
 
 def footprint(n_envs: int, n_roms: int, **cfg) -> int:
@@ -277,8 +278,9 @@ class AtariEnv:
                                           ring_planes.shape[0], ring_start, _stream(stream)))
 
     def launch_shape(self):
-        """(envs per warp, envs per block, warps per frame, interpreter grid)."""
-        v = [C.c_int() for _ in range(4)]
+        """(envs per warp, envs per block, warps per frame, interpreter grid,
+        tia_warps: 2 with paired TIA warps, else 1)."""
+        v = [C.c_int() for _ in range(5)]
         _check(self.lib.atari_env_launch_shape(self.h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
 

@@ -66,6 +66,11 @@ FORMS = {
     "batched-32x128-w4": dict(form=FORM_BATCHED, envs_per_warp=32, envs_per_block=128, raster_warps_per_frame=4),
     "batched-8x16-w1": dict(form=FORM_BATCHED, envs_per_warp=8, envs_per_block=16, raster_warps_per_frame=1),
     "batched-1x4-w2": dict(form=FORM_BATCHED, envs_per_warp=1, envs_per_block=4, raster_warps_per_frame=2),
+    # paired CPU / TIA warps
+    "split-32x128-w4": dict(form=FORM_BATCHED, envs_per_warp=32, envs_per_block=128, raster_warps_per_frame=4,
+                            tia_warps=2),
+    "split-8x16-w2": dict(form=FORM_BATCHED, envs_per_warp=8, envs_per_block=16, raster_warps_per_frame=2,
+                          tia_warps=2),
 }
 
 
@@ -95,7 +100,7 @@ def test_cache_matches_oracle():
         assert_same("cache", g.cache().cpu().numpy(), o.cache())
 
 
-@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-1x4-w2"])
+@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-1x4-w2", "split-8x16-w2"])
 def test_playfield_full_tiny_config(form):
     """16 envs of one 4 KB playfield cartridge, 250 steps x 4 frames, palette
     frames out: every output (and, in the plain form, both rendered frames)
@@ -113,11 +118,13 @@ def test_sprite_family_stack_output(form):
     the 84x84x4 stack."""
     w = synth.workload(2, n_envs=96)
     g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=w.seed, **FORMS[form])
+    if form.startswith("split"):
+        assert g.launch_shape()[4] == 2      # the paired CPU / TIA warp kernel runs
     acts = synth.actions(12, 120, 96)
     run_parity(g, o, acts, check_frames=True, check_state_every=1)
 
 
-@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-8x16-w1"])
+@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-8x16-w1", "split-8x16-w2"])
 def test_banked_sticky_family(form):
     """32 cartridges mixing 4 KB, F8 and F6 with code in every bank, RIOT-timer
     frame timing and sticky actions drawn from the per-env Philox stream."""
@@ -127,7 +134,8 @@ def test_banked_sticky_family(form):
     run_parity(g, o, acts, check_frames=True)
 
 
-@pytest.mark.parametrize("seed0,form", [(0, "plain"), (8, "plain"), (0, "batched-auto"), (16, "batched-8x16-w1")])
+@pytest.mark.parametrize("seed0,form", [(0, "plain"), (8, "plain"), (0, "batched-auto"), (16, "batched-8x16-w1"),
+                                        (24, "split-32x128-w4")])
 def test_fuzz_programs(seed0, form):
     """Random-program cartridges (all documented opcodes, decimal mode, RMW on
     TIA strobes, TIA/RIOT reads, halting opcodes) stepped on both sides."""
@@ -162,7 +170,8 @@ def test_full_size_sprite_config_sampled(form):
     assert int(g.status().abs().sum().item()) == 0
 
 
-@pytest.mark.parametrize("n,form", [(1, "plain"), (37, "plain"), (1, "batched-auto"), (37, "batched-32x128-w4")])
+@pytest.mark.parametrize("n,form", [(1, "plain"), (37, "plain"), (1, "batched-auto"), (37, "batched-32x128-w4"),
+                                    (37, "split-32x128-w4")])
 def test_ragged_and_single(n, form):
     w = synth.workload(2, n_envs=n)
     g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, seed=9, **FORMS[form])
