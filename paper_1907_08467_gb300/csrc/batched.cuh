@@ -153,7 +153,7 @@ __device__ void tia_worker(IoCtx c, const uint32_t *q, int i, const BatchArgs &a
         c.Sset(IO_STATUS, c.G(IO_STATUS) | ST_STALL);
         break;
       }
-      __nanosleep(32);
+      __nanosleep(128);  // an idle TIA lane polls gently: the CPU warps share the SM's memory pipe
       continue;
     }
     spins = 0;

@@ -387,7 +387,7 @@ struct FastConsoleT {
   uint32_t wmask;          // lanes of this warp running envs (lockstep issue)
   // split form: this env's TIA event queue and the CPU side's copies
   uint32_t *q;
-  uint32_t qtail, nreq, vsync_c, vblank_c, broken;
+  uint32_t qtail, qhead_seen, nreq, vsync_c, vblank_c, broken;  // qhead_seen: the TIA side's cursor as last read
   uint64_t l0c;
 
   __device__ __forceinline__ uint32_t P() const {
@@ -441,7 +441,7 @@ struct FastConsoleT {
       vsync_c = io.T(T_VSYNC);
       vblank_c = io.T(T_VBLANK);
       l0c = L0;
-      qtail = nreq = broken = 0;
+      qtail = qhead_seen = nreq = broken = 0;
       io.Sset(IO_QHEAD, 0); io.Sset(IO_QTAIL, 0); io.Sset(IO_ACK, 0);
     }
   }
@@ -537,13 +537,16 @@ struct FastConsoleT {
     status |= ST_STALL;
     jam = 1;
   }
-  // Append an event (waits, bounded, while the queue is full).
+  // Append an event (waits, bounded, while the queue is full).  The TIA
+  // side's cursor is reread only when the queue looks full.
   __device__ __forceinline__ void push(uint32_t ev) {
     if (broken) return;
-    uint32_t spins = 0;
-    while (qtail - *vio(IO_QHEAD) >= QLEN) {
-      if (++spins > SPIN_LIMIT) { stall(); return; }
-      __nanosleep(32);
+    if (qtail - qhead_seen >= QLEN) {
+      uint32_t spins = 0;
+      while (qtail - (qhead_seen = *vio(IO_QHEAD)) >= QLEN) {
+        if (++spins > SPIN_LIMIT) { stall(); return; }
+        __nanosleep(32);
+      }
     }
     reinterpret_cast<volatile uint32_t *>(q)[qtail & (QLEN - 1)] = ev;
     __threadfence_block();
@@ -1091,7 +1094,7 @@ __device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT> *self) {
   self->bank = tmp.bank; self->jam = tmp.jam; self->kf = tmp.kf; self->pend = tmp.pend; self->vs_kf = tmp.vs_kf;
   self->status = tmp.status; self->instret = tmp.instret; self->frame_no = tmp.frame_no;
   if constexpr (SPLIT) {
-    self->qtail = tmp.qtail; self->nreq = tmp.nreq; self->vsync_c = tmp.vsync_c; self->vblank_c = tmp.vblank_c;
+    self->qtail = tmp.qtail; self->qhead_seen = tmp.qhead_seen; self->nreq = tmp.nreq; self->vsync_c = tmp.vsync_c; self->vblank_c = tmp.vblank_c;
     self->broken = tmp.broken; self->l0c = tmp.l0c;
   }
 }
