@@ -88,7 +88,8 @@ typedef struct {
     uint64_t seed;        /* Philox4x32-10 key for start states, resets and sticky draws */
     int tia_warps;        /* batched form: 1 = each warp runs its envs' CPU and TIA; 2 = a TIA warp per
                              CPU warp takes the TIA writes, logging and collisions off the CPU's
-                             path; 0 = autotune */
+                             path; 0 = autotune; 3 = as 2 with the TIA side switched off, to test the
+                             bounded waits (every env ends its steps with ATARI_ST_STALL) */
 } atari_config;
 
 /* Fill *cfg with the paper's defaults: F = 4, no sticky actions, 30 cached

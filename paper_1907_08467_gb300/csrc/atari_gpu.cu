@@ -503,9 +503,9 @@ int validate(const atari_config &c) {
   if (c.log_cap < 256 || c.log_cap > (1 << 20)) return fail(ATARI_EINVAL, "log_cap must be in 256..2^20");
   if (c.sticky != 0 && c.sticky != 1) return fail(ATARI_EINVAL, "sticky must be 0 or 1");
   if (c.envs_per_block < 0 || c.envs_per_block > 128 || c.envs_per_warp < 0 || c.envs_per_warp > 32 ||
-      c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4 || c.tia_warps < 0 || c.tia_warps > 2)
+      c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4 || c.tia_warps < 0 || c.tia_warps > 3)
     return fail(ATARI_EINVAL, "envs_per_block must be 0..128, envs_per_warp 0..32, raster_warps_per_frame 0..4, "
-                              "tia_warps 0..2");
+                              "tia_warps 0..3");
   return 0;
 }
 
@@ -597,6 +597,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
   a.log_cap = c.log_cap;
   a.first_slot = c.output_mode == ATARI_OUT_PALETTE ? 1 : 0;
   a.seed = c.seed;
+  a.tia_off = c.tia_warps == 3 ? 1 : 0;
   return a;
 }
 
@@ -733,6 +734,10 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
     if ((rc = dalloc(&E->d_ring, n * 4 * 7056, T)) || (rc = dalloc(&E->d_head, n, T))) return bail(rc);
     if (c.form == ATARI_FORM_BATCHED && (rc = dalloc(&E->d_bsnap, n * 2 * 3 * 64, T))) return bail(rc);
   }
+  // render inputs start zeroed (a step that failed to write them still renders defined values)
+  if (n && (cudaMemset(E->d_snap, 0, n * 2 * 64) != cudaSuccess || cudaMemset(E->d_meta, 0, n * 2 * 2 * 4) != cudaSuccess ||
+            (E->d_bsnap && cudaMemset(E->d_bsnap, 0, n * 2 * 3 * 64) != cudaSuccess)))
+    return bail(fail(ATARI_ECUDA, "zeroing render buffers failed"));
 
   // cartridges: 2K images mirrored to 4K, each in a 16 KB slot
   std::vector<uint8_t> img((size_t)n_roms * ROM_SLOT, 0);
@@ -977,7 +982,7 @@ int autotune(atari_env *E) {
   for (int ci = 0; ci < (int)(sizeof cand / sizeof cand[0]); ++ci) {
     const auto &c = cand[ci];
     if ((size_t)c[0] * c[1] > 4 * n && c[0] * c[1] > 32) continue;  // far more slots than envs
-    if ((E->cfg.tia_warps == 1 && c[2]) || (E->cfg.tia_warps == 2 && !c[2])) continue;
+    if ((E->cfg.tia_warps == 1 && c[2]) || (E->cfg.tia_warps >= 2 && !c[2])) continue;
     if (int rc = build_groups(E, c[0], c[1], c[2] != 0)) { cudaFree(st_bak); return rc; }
     BatchArgs a = batch_args(E, E->d_act, nullptr, nullptr);
     float t = 0;
@@ -995,7 +1000,7 @@ int autotune(atari_env *E) {
   }
   float best = 1e30f;
   for (auto &p : timed) best = std::min(best, p.first);
-  int bl = 32, bw = 4, bs = E->cfg.tia_warps == 2 ? 1 : 0;
+  int bl = 32, bw = 4, bs = E->cfg.tia_warps >= 2 ? 1 : 0;
   for (auto &p : timed)
     if (p.first <= 1.03f * best) { bl = cand[p.second][0]; bw = cand[p.second][1]; bs = cand[p.second][2]; break; }
   int rc = build_groups(E, bl, bw, bs != 0);
@@ -1064,9 +1069,9 @@ int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vect
   if (c.envs_per_block > 0 && c.envs_per_warp > 0) {
     int L = std::min(32, c.envs_per_warp), W = std::max(1, std::min(4, c.envs_per_block / L));
     E->wpf = c.raster_warps_per_frame > 0 ? c.raster_warps_per_frame : 4;
-    return build_groups(E, L, W, c.tia_warps == 2);
+    return build_groups(E, L, W, c.tia_warps >= 2);
   }
-  if (E->n == 0) return build_groups(E, 32, 4, c.tia_warps == 2);
+  if (E->n == 0) return build_groups(E, 32, 4, c.tia_warps >= 2);
   return autotune(E);
 }
 }  // namespace

@@ -43,6 +43,7 @@ struct BatchArgs {
   int *queue;
   int n_groups, lanes, E, rom_stage;  // rom_stage: bytes staged per block (largest cartridge)
   int frameskip, sticky, n_cache, log_cap, first_slot;
+  int tia_off;               // split form test mode: the TIA side takes no events
   uint64_t seed;
 };
 
@@ -144,6 +145,7 @@ __device__ __forceinline__ void fast_step_env(FastConsoleT<SPLIT> &m, uint8_t *s
 // order until the end of the step.  Every wait is bounded; running out sets
 // ST_STALL and ends the loop.
 __device__ void tia_worker(IoCtx c, const uint32_t *q, int i, const BatchArgs &a) {
+  if (a.tia_off) return;
   volatile uint32_t *vw = reinterpret_cast<volatile uint32_t *>(c.w());
   const volatile uint32_t *vq = reinterpret_cast<const volatile uint32_t *>(q);
   uint32_t head = 0, ack = 0, lines = 0, log_total = 0, spins = 0;

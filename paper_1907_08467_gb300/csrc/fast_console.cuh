@@ -363,7 +363,8 @@ constexpr uint32_t QSTRIDE = QLEN + 1;    // shared-memory words per env queue (
 constexpr uint32_t EV_WRITE = 0u, EV_FRAME_END = 1u << 30, EV_CTRL = 2u << 30;
 constexpr uint32_t EV_BEGIN_LOG = EV_CTRL, EV_END_LOG = EV_CTRL | 1u << 28, EV_SYNC = EV_CTRL | 2u << 28,
                    EV_STEP_END = EV_CTRL | 3u << 28;
-constexpr uint32_t SPIN_LIMIT = 1u << 22;  // polls of a queue cursor before the env is declared stalled
+constexpr uint32_t SPIN_LIMIT = 1u << 20;  // polls (each after a short sleep) before the env is declared stalled;
+                                           // far above the longest legitimate wait, about a frame of the partner
 // registers whose writes reach the TIA side (WSYNC, RSYNC, audio and unused
 // addresses change nothing there)
 constexpr uint64_t SPLIT_PUSH_REGS = LOG_REGS | COLL_REGS | 1ull | (1ull << 0x2C);

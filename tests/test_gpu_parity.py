@@ -307,3 +307,25 @@ def test_full_size_banked_config_sampled():
         assert_same(f"step {s} obs", obs.cpu().numpy()[idx], oo)
     assert_same("state", g.state().cpu().numpy()[idx], o.state())
     assert int(g.status().abs().sum().item()) == 0
+
+
+def test_split_form_bounded_waits_report_stall():
+    """With the TIA side switched off (tia_warps 3) every queue wait of the
+    CPU warps runs out: the step still returns, every env reports ST_STALL
+    (and halts), and the context stays usable for a normal env afterwards."""
+    import time
+    from paper_1907_08467_gb300.env import ST_STALL
+    w = synth.workload(2, n_envs=8)
+    g = AtariEnv.from_workload(w, form=FORM_BATCHED, envs_per_warp=8, envs_per_block=8, raster_warps_per_frame=1,
+                               tia_warps=3)
+    assert g.launch_shape()[4] == 2
+    t0 = time.time()
+    g.step(torch.zeros(8, dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 60
+    st = g.status().cpu().numpy().astype(np.int64)
+    assert ((st & ST_STALL) != 0).all(), st
+    g.close()
+    # the context is intact: a normal env still matches the oracle
+    g2, o = pair(w.roms, w.env_rom, seed=w.seed, **FORMS["split-8x16-w2"])
+    run_parity(g2, o, synth.actions(41, 3, 8))
