@@ -370,6 +370,30 @@ constexpr uint32_t SPIN_LIMIT = 1u << 20;  // polls (each after a short sleep) b
 constexpr uint64_t SPLIT_PUSH_REGS = LOG_REGS | COLL_REGS | 1ull | (1ull << 0x2C);
 
 // ---------------------------------------------------------------- the console
+// Split form, CPU side: bounded waits on the TIA side's cursors in this env's
+// I/O block.  Wait until the queue has room behind `qtail` (returns the last
+// head read: still full means the wait ran out), or until `n` events are
+// acknowledged (false means the wait ran out).
+__device__ __noinline__ uint32_t fc_q_wait_room(uint32_t *iow, uint32_t qtail) {
+  __builtin_assume(__isShared(iow));
+  const volatile uint32_t *h = iow + IO_QHEAD;
+  uint32_t head = *h;
+  for (uint32_t spins = 0; qtail - head >= QLEN && spins < SPIN_LIMIT; ++spins) {
+    __nanosleep(32);
+    head = *h;
+  }
+  return head;
+}
+__device__ __noinline__ bool fc_q_wait_ack(uint32_t *iow, uint32_t n) {
+  __builtin_assume(__isShared(iow));
+  const volatile uint32_t *a = iow + IO_ACK;
+  for (uint32_t spins = 0; (int32_t)(*a - n) < 0; ++spins) {
+    if (spins >= SPIN_LIMIT) return false;
+    __nanosleep(32);
+  }
+  return true;
+}
+
 template <bool SPLIT> struct FastConsoleT;
 template <bool SPLIT> __device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT> *self);
 
@@ -539,15 +563,13 @@ struct FastConsoleT {
     jam = 1;
   }
   // Append an event (waits, bounded, while the queue is full).  The TIA
-  // side's cursor is reread only when the queue looks full.
+  // side's cursor is reread only when the queue looks full; the waits run out
+  // of line so that each inlined push stays small.
   __device__ __forceinline__ void push(uint32_t ev) {
     if (broken) return;
     if (qtail - qhead_seen >= QLEN) {
-      uint32_t spins = 0;
-      while (qtail - (qhead_seen = *vio(IO_QHEAD)) >= QLEN) {
-        if (++spins > SPIN_LIMIT) { stall(); return; }
-        __nanosleep(32);
-      }
+      qhead_seen = fc_q_wait_room(io.w(), qtail);
+      if (qtail - qhead_seen >= QLEN) { stall(); return; }
     }
     reinterpret_cast<volatile uint32_t *>(q)[qtail & (QLEN - 1)] = ev;
     __threadfence_block();
@@ -557,11 +579,7 @@ struct FastConsoleT {
   // Wait (bounded) until the TIA side has acknowledged n events.
   __device__ __forceinline__ void wait_ack(uint32_t n) {
     if (broken) return;
-    uint32_t spins = 0;
-    while ((int32_t)(*vio(IO_ACK) - n) < 0) {
-      if (++spins > SPIN_LIMIT) { stall(); return; }
-      __nanosleep(32);
-    }
+    if (!fc_q_wait_ack(io.w(), n)) { stall(); return; }
     __threadfence_block();
   }
   // TIA write in the split form: WSYNC, the VSYNC rise and the VBLANK latch
@@ -1046,29 +1064,31 @@ struct FastConsoleT {
   // it, so the warp reconverges on code rather than on time (lanes a few
   // cycles apart after a page-crossing or a different branch path still run
   // together), and the executing lanes take one case of the opcode switch.
-  // The leader always advances (every instruction takes at least 2 cycles,
-  // and a frame ends after at most 400 lines), so the loop ends.
+  // One warp reduction elects the leader: the minimum of (cycle << 16 | PC)
+  // over the active lanes gives its PC directly (ties in the cycle go to the
+  // smaller PC), and all-ones means no lane is active.  The cycle saturates
+  // below 0xFFFF, so the key always names a lane's actual PC.  The leader
+  // always advances (every instruction takes at least 2 cycles, and a frame
+  // ends after at most 400 lines), so the loop ends.
   __device__ __forceinline__ uint32_t run_frame() {
     uint32_t next_rel = 0;
     vs_kf = ~0u;
-    bool active = true;
-    while (__any_sync(wmask, active)) {
-      // next instruction word, fetched before the vote so the two latencies overlap
+    bool active = !jam;
+    if (jam) next_rel = kf / 76u;
+    for (;;) {
+      // next instruction word, fetched before the election so the two latencies overlap
       // (bank < banks of the staged cartridge, so the index stays in the stage)
       const uint32_t w = fetch4(bank * 4096u + (PC & 0xFFFu));
-      const uint32_t mine = active ? kf : 0xFFFFFFFFu;
-      const uint32_t lead = __reduce_min_sync(wmask, mine);
-      const uint32_t first = __ffs(__ballot_sync(wmask, active && kf == lead)) - 1;
-      const uint32_t lpc = __shfl_sync(wmask, PC, first);
-      if (active && PC == lpc) {
-        if (jam) {
-          next_rel = kf / 76u;
+      const uint32_t key = active ? (min(kf, 0xFFFEu) << 16 | (PC & 0xFFFFu)) : 0xFFFFFFFFu;
+      const uint32_t lead = __reduce_min_sync(wmask, key);
+      if (lead == 0xFFFFFFFFu) break;
+      if (active && PC == (lead & 0xFFFFu)) {
+        if (!exec(w)) fc_exec_general<SPLIT>(this);
+        if (jam | (vs_kf != ~0u) | (kf >= 76u * CAP_LINES)) {
+          if (jam) next_rel = kf / 76u;
+          else if (vs_kf != ~0u) next_rel = vs_kf / 76u;
+          else { status |= ST_FRAME_CAP; next_rel = kf / 76u; }
           active = false;
-        } else {
-          if (!exec(w)) fc_exec_general<SPLIT>(this);
-          if (jam) { next_rel = kf / 76u; active = false; }
-          else if (vs_kf != ~0u) { next_rel = vs_kf / 76u; active = false; }
-          else if (kf >= 76u * CAP_LINES) { status |= ST_FRAME_CAP; next_rel = kf / 76u; active = false; }
         }
       }
     }
