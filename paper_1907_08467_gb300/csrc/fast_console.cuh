@@ -394,6 +394,40 @@ __device__ __noinline__ bool fc_q_wait_ack(uint32_t *iow, uint32_t n) {
   return true;
 }
 
+// Split form, CPU side: read a TIA or RIOT address (13-bit, neither RAM nor
+// cartridge) at cycle t, out of line so that the many read sites of the
+// opcode switch stay small.  A collision-latch read first pushes a sync event
+// at queue position qtail (waiting, bounded, for room behind the TIA side's
+// cursor qhead_seen) and waits until the TIA side has acknowledged nreq + 1
+// sync events, i.e. has evaluated collisions up to cycle t.  Returns the
+// value in bits 0-7; bit 8 when the sync event was pushed (the caller counts
+// it, and the queue is then empty), bit 9 when a wait ran out (the caller
+// halts the env).  `broken` (an earlier wait ran out) skips the sync and
+// returns the latches as they stand.
+constexpr uint32_t SIO_PUSHED = 0x100u, SIO_STALL = 0x200u;
+__device__ __noinline__ uint32_t fc_split_io_read(IoCtx c, uint32_t *q, uint32_t qtail, uint32_t qhead_seen,
+                                                  uint32_t nreq, uint32_t broken, uint32_t a, uint32_t t,
+                                                  uint64_t l0) {
+  if (a & 0x80) return fc_riot_read(c, a, 76ull * l0 + t);
+  const uint32_t reg = a & 0x0F;
+  if (reg == 0x0C) return (c.G(IO_FIRE) || c.G(IO_LATCH)) ? 0x00u : 0x80u;
+  if (reg == 0x0D) return 0x80u;
+  if (reg >= 8) return 0;
+  volatile uint32_t *vw = reinterpret_cast<volatile uint32_t *>(c.w());
+  if (broken) return fc_cx_byte(vw[IO_CX], reg);
+  if (qtail - qhead_seen >= QLEN) {
+    qhead_seen = fc_q_wait_room(c.w(), qtail);
+    if (qtail - qhead_seen >= QLEN) return SIO_STALL | fc_cx_byte(vw[IO_CX], reg);
+  }
+  __builtin_assume(__isShared(q));
+  reinterpret_cast<volatile uint32_t *>(q)[qtail & (QLEN - 1)] = EV_SYNC | (t & 0xFFFFu);
+  __threadfence_block();
+  vw[IO_QTAIL] = qtail + 1;
+  if (!fc_q_wait_ack(c.w(), nreq + 1)) return SIO_PUSHED | SIO_STALL | fc_cx_byte(vw[IO_CX], reg);
+  __threadfence_block();
+  return SIO_PUSHED | fc_cx_byte(vw[IO_CX], reg);
+}
+
 template <bool SPLIT> struct FastConsoleT;
 template <bool SPLIT> __device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT> *self);
 
@@ -601,18 +635,10 @@ struct FastConsoleT {
     if constexpr (!SPLIT) {
       return fc_io_read(io, a, t);
     } else {
-      if (!(a & 0x80)) {
-        const uint32_t reg = a & 0x0F;
-        if (reg < 8) {  // collision latches: the TIA side evaluates them up to this cycle first
-          push(EV_SYNC | (t & 0xFFFFu));
-          wait_ack(++nreq);
-          return fc_cx_byte(*vio(IO_CX), reg);
-        }
-        if (reg == 0x0C) return (io.G(IO_FIRE) || io.G(IO_LATCH)) ? 0x00u : 0x80u;
-        if (reg == 0x0D) return 0x80u;
-        return 0;
-      }
-      return fc_riot_read(io, a, 76ull * l0c + t);
+      const uint32_t r = fc_split_io_read(io, q, qtail, qhead_seen, nreq, broken, a, t, l0c);
+      if (r & SIO_PUSHED) { ++qtail; ++nreq; qhead_seen = qtail; }
+      if (r & SIO_STALL) stall();
+      return r & 0xFFu;
     }
   }
   __device__ __forceinline__ void io_write(uint32_t a, uint32_t v, uint32_t t) {
@@ -772,27 +798,23 @@ struct FastConsoleT {
                const uint32_t base = ram[b1 & 0x7F] | ram[(b1 + 1) & 0x7F] << 8;                  \
                const uint32_t ea = (base + Y) & 0xFFFF; n = 5 + XPG(base, ea);                                \
                const uint32_t v = rd(ea, k0 + n - 1); BODY; PC = pc + 2; break; }
-// read-modify-write: acc, zp, zp,X, abs, abs,X
+// read-modify-write: acc, zp, zp,X, abs, abs,X.  The memory forms take RAM
+// here (where the old-value write is invisible); a TIA, RIOT or cartridge
+// address goes to the general decoder, which models both writes.
+#define RMW_MEM_OPS(OPZ, OPZX, OPA, OPAX, FN)                                                                \
+  case OPZ: { if (!(b1 & 0x80)) return false;                                                                 \
+              ram[b1 & 0x7F] = FN(ram[b1 & 0x7F]); n = 5; PC = pc + 2; break; }                              \
+  case OPZX: { const uint32_t z = ZPX_; if (!(z & 0x80)) return false;                                        \
+               ram[z & 0x7F] = FN(ram[z & 0x7F]); n = 6; PC = pc + 2; break; }                                \
+  case OPA: { if ((a16 & 0x1280) != 0x0080) return false;                                                     \
+              ram[a16 & 0x7F] = FN(ram[a16 & 0x7F]); n = 6; PC = pc + 3; break; }                            \
+  case OPAX: { const uint32_t ea = ABX_; if ((ea & 0x1280) != 0x0080) return false;                          \
+               ram[ea & 0x7F] = FN(ram[ea & 0x7F]); n = 7; PC = pc + 3; break; }
 #define RMW_OPS(OPACC, OPZ, OPZX, OPA, OPAX, FN)                                                             \
   case OPACC: { A = FN(A); n = 2; PC = pc + 1; break; }                                                       \
-  case OPZ: { const uint32_t o = rdz(b1, k0 + 2); const uint32_t r = FN(o);                                   \
-              wrz(b1, o, k0 + 3); wrz(b1, r, k0 + 4); n = 5; PC = pc + 2; break; }                            \
-  case OPZX: { const uint32_t z = ZPX_; const uint32_t o = rdz(z, k0 + 3); const uint32_t r = FN(o);          \
-               wrz(z, o, k0 + 4); wrz(z, r, k0 + 5); n = 6; PC = pc + 2; break; }                             \
-  case OPA: { const uint32_t o = rd(a16, k0 + 3); const uint32_t r = FN(o);                                   \
-              wr(a16, o, k0 + 4); wr(a16, r, k0 + 5); n = 6; PC = pc + 3; break; }                            \
-  case OPAX: { const uint32_t ea = ABX_; const uint32_t o = rd(ea, k0 + 4); const uint32_t r = FN(o);         \
-               wr(ea, o, k0 + 5); wr(ea, r, k0 + 6); n = 7; PC = pc + 3; break; }
+  RMW_MEM_OPS(OPZ, OPZX, OPA, OPAX, FN)
 // memory-only read-modify-write (INC, DEC): zp, zp,X, abs, abs,X
-#define RMWM_OPS(OPZ, OPZX, OPA, OPAX, FN)                                                                   \
-  case OPZ: { const uint32_t o = rdz(b1, k0 + 2); const uint32_t r = FN(o);                                   \
-              wrz(b1, o, k0 + 3); wrz(b1, r, k0 + 4); n = 5; PC = pc + 2; break; }                            \
-  case OPZX: { const uint32_t z = ZPX_; const uint32_t o = rdz(z, k0 + 3); const uint32_t r = FN(o);          \
-               wrz(z, o, k0 + 4); wrz(z, r, k0 + 5); n = 6; PC = pc + 2; break; }                             \
-  case OPA: { const uint32_t o = rd(a16, k0 + 3); const uint32_t r = FN(o);                                   \
-              wr(a16, o, k0 + 4); wr(a16, r, k0 + 5); n = 6; PC = pc + 3; break; }                            \
-  case OPAX: { const uint32_t ea = ABX_; const uint32_t o = rd(ea, k0 + 4); const uint32_t r = FN(o);         \
-               wr(ea, o, k0 + 5); wr(ea, r, k0 + 6); n = 7; PC = pc + 3; break; }
+#define RMWM_OPS(OPZ, OPZX, OPA, OPAX, FN) RMW_MEM_OPS(OPZ, OPZX, OPA, OPAX, FN)
 #define BR(OPC, COND)                                                                                          \
   case OPC: {                                                                                                 \
     const uint32_t nx = (pc + 2) & 0xFFFF;                                                                    \
@@ -903,6 +925,7 @@ struct FastConsoleT {
 #undef XPG
 #undef NZ
 #undef RD_OPS
+#undef RMW_MEM_OPS
 #undef RMW_OPS
 #undef RMWM_OPS
 #undef BR
