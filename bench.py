@@ -38,9 +38,8 @@ SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 # 16384 env-frames / 4096 env-steps), keyed by (workload config, form, envs
 # per warp, tia_warps).  They hold for the interpreter version captured there; a key
 # without an entry reports achieved = null.
-INTERP_WARP_INST_PER_ENV_FRAME = {(2, "batched", 32, 1): 416831777 / 16384, (2, "batched", 32, 2): 429668343 / 16384}
-INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 32, 1): (1278720 + 131840) / 4096,
-                                  (2, "batched", 32, 2): (1313792 + 129280) / 4096}
+INTERP_WARP_INST_PER_ENV_FRAME = {(2, "batched", 32, 2): 424750280 / 16384}
+INTERP_DRAM_BYTES_PER_ENV_STEP = {(2, "batched", 32, 2): (1278720 + 112128) / 4096}
 # Algorithmic bytes of the fused rasterise + preprocess kernel per env-step,
 # besides 4 bytes per logged TIA write: snapshots and record counts of the two
 # rendered frames (2 x 64 + 2 x 8), the three older stack planes read from the
