@@ -13,7 +13,7 @@
  *   - Section 4 (memory discussion): four stacked 84x84 frames per env.
  *
  * The machine behaviour is the public definition of the console, with these
- * readings where the paper is silent (each is listed in the design doc):
+ * readings where the paper is silent:
  *   R1  a frame ends when a VSYNC write takes D1 from 0 to 1 (the writing
  *       instruction completes), or at the first instruction boundary 400
  *       lines after the frame's first line (status FRAME_CAP).

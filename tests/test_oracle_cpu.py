@@ -93,6 +93,37 @@ def test_decimal_examples_from_description():
     assert alu_sbc(0x12, 0x21, D | C) & 0x1FF == 0x91
 
 
+# Decimal-mode ADC flags worked by hand from reading R13 (B. Clark's NMOS
+# description): A and C from the nibble-adjusted sum; Z from the binary sum;
+# N and V from the intermediate sum taken before the high-nibble adjustment,
+# with the high nibbles as signed bytes: low = (A & $0F) + (B & $0F) + C,
+# low >= $0A -> ((low + 6) & $0F) + $10; s = (int8)(A & $F0) + (int8)(B & $F0)
+# + low; N = bit 7 of s, V = s outside -128..127.
+#     A + B + C     A'  C  Z  N  V   intermediate s
+DECIMAL_ADC_WORKED = [
+    (0x99, 0x00, 1, 0x00, 1, 0, 1, 0),   # -112 + 0 + 16 = -96 ($A0): N set although A' = $00
+    (0x79, 0x00, 1, 0x80, 0, 0, 1, 1),   # 112 + 0 + 16 = 128: V set although the binary $7A has none
+    (0x50, 0x50, 0, 0x00, 1, 0, 1, 1),   # 80 + 80 + 0 = 160 ($A0)
+    (0x90, 0x90, 0, 0x80, 1, 0, 0, 1),   # -112 - 112 + 0 = -224 ($20): N clear although A' = $80
+    (0x99, 0x01, 0, 0x00, 1, 0, 1, 0),   # -112 + 0 + 16 = -96; Z from the binary $9A
+    (0x00, 0x00, 0, 0x00, 0, 1, 0, 0),
+    (0x19, 0x28, 0, 0x47, 0, 0, 0, 0),   # low 17 -> 23; 16 + 32 + 23 = 71
+    (0x45, 0x45, 0, 0x90, 0, 0, 1, 1),   # 64 + 64 + 16 = 144
+]
+
+
+def test_decimal_adc_n_and_v_worked_cases():
+    """N and V of decimal ADC, worked by hand (table above).  Catches N taken
+    from the final byte (rows 1, 3, 4, 5), V taken from the binary sum (row
+    2), and N/V taken after the +$60 adjustment (rows 1, 3)."""
+    for a, b, c, ea, ec, ez, en, ev in DECIMAL_ADC_WORKED:
+        r = alu_adc(a, b, D | c)
+        p = r >> 8
+        got = (r & 0xFF, int(bool(p & C)), int(bool(p & Z)), int(bool(p & N)), int(bool(p & V)))
+        assert got == (ea, ec, ez, en, ev), (hex(a), hex(b), c, got)
+        assert p & D
+
+
 def test_documented_opcode_set():
     """Exactly the 151 documented opcodes have a cycle count; the other 105 JAM."""
     doc = {op for modes in OPCODES.values() for op in modes.values()}
