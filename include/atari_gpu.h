@@ -116,11 +116,23 @@ ATARI_API int atari_env_create(const uint8_t *const *roms, const size_t *rom_siz
 /*
  * Force a reset of the envs whose d_mask byte is nonzero (d_mask NULL: all):
  * episode += 1, state <- cached start state, frame stack zeroed.
+ * Paper, Section 3 (reset strategy): at the end of an episode an emulator
+ * copies a randomly chosen cached start state into its terminal state, in
+ * place of running 64 start-up frames and up to 30 random no-op frames.  The
+ * cached state is cache[rom][mulhi32(philox(seed, env_key, 0, 2 << 8,
+ * episode), n_cache)] with the incremented episode.  d_mask (device, n bytes)
+ * is read on `stream`; NULL env returns ATARI_EINVAL.
  */
 ATARI_API int atari_env_reset(atari_env *env, const uint8_t *d_mask, atari_stream stream);
 
 /*
- * One step of every env: d_actions[i] (device, uint8, ALE action 0..17) is
+ * One step of every env.  Paper, Section 1 (the inference path: environments
+ * take an action set and return the next observable states and rewards),
+ * Section 1 footnote (frame skip 4, every emulated frame counted) and
+ * Section 3 (only the last two frames of the four are rendered; the agent's
+ * input is their pixelwise maximum; finished episodes restart from the
+ * cache of start states).
+ * d_actions[i] (device, uint8, ALE action 0..17) is
  * applied for F frames (sticky repeats drawn per frame when enabled).
  * Writes d_obs (layout per output_mode), d_rewards[i] (int32: sum over the F
  * frames of the int8 change of the score byte) and d_dones[i] (uint8: the
@@ -133,7 +145,8 @@ ATARI_API int atari_env_step(atari_env *env, const uint8_t *d_actions, uint8_t *
                    uint8_t *d_dones, atari_stream stream);
 
 /*
- * Same step with host buffers: copies actions host->device, steps, and
+ * Same step with host buffers (the host round trip of Section 1's inference
+ * path, for callers whose agent runs on the host): copies actions host->device, steps, and
  * copies obs / rewards / dones device->host on `stream`, then synchronises
  * the stream.  Host pointers may be pageable or pinned; NULL skips.
  */
@@ -169,14 +182,25 @@ ATARI_API int atari_env_rollout(atari_env *env, const uint16_t *d_weights, int n
                                 uint8_t *d_actions, int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes,
                                 float *d_ring_rewards, int ring_depth, int ring_start, atari_stream stream);
 
-/* d_status (device, uint32 [n]) <- per-env status bits. */
+/* d_status (device, uint32 [n]) <- per-env status bits (ATARI_ST_*), on
+ * `stream`.  The paper is silent on machine faults; here they never fail a
+ * call: an undocumented opcode halts that env's CPU (done at step end), a
+ * frame longer than 400 lines ends at the cap, a log overflow truncates that
+ * frame's rendering, an out-of-range action runs as NOOP, and a split-form
+ * wait that runs out halts the env.  Each sets its bit for the life of the
+ * env.  NULL env or d_status returns ATARI_EINVAL. */
 ATARI_API int atari_env_status(atari_env *env, uint32_t *d_status, atari_stream stream);
 
 /*
  * Canonical per-env state, 256 bytes per env, little-endian (layout in the
- * table below).  get copies n*256 bytes to d_dst; set loads them from d_src.
- * A saved state restores a run exactly: the random streams are keyed by
- * fields inside it.
+ * table below).  get copies n*256 bytes to d_dst; set loads them from d_src
+ * (both device buffers owned by the caller, copied on `stream`).  The paper
+ * keeps each console's CPU state and its 128 bytes of RAM in device memory
+ * (Section 3) but defines no save/restore; this layout is the library's
+ * own.  A saved state restores a run exactly: the random streams are keyed
+ * by fields inside it.  A bank byte with bits the cartridge does not latch
+ * is reduced to the cartridge's bits when the state is next stepped.  NULL
+ * env or buffer returns ATARI_EINVAL.
  *
  *   0x00 A  0x01 X  0x02 Y  0x03 SP  0x04 P (bit 5 set, B clear)  0x05 bank
  *   0x06 u16 PC   0x08 u64 CPU cycle   0x10 u64 RIOT timer write cycle
@@ -202,7 +226,9 @@ ATARI_API int atari_env_set_state(atari_env *env, const void *d_src, atari_strea
  * (the batched form never materialises frames); ATARI_EINVAL otherwise. */
 ATARI_API int atari_env_get_frames(atari_env *env, uint8_t *d_dst, atari_stream stream);
 
-/* d_dst <- the start-state cache, [n_roms][n_cache][256] canonical states. */
+/* d_dst <- the start-state cache, [n_roms][n_cache][256] canonical states
+ * (the cache of random initial states of Section 3's reset strategy).
+ * Device buffer owned by the caller, copied on `stream`. */
 ATARI_API int atari_env_get_cache(atari_env *env, void *d_dst, atari_stream stream);
 
 /* Counters of the last step: 6502 instructions retired (sum over envs) and
@@ -237,10 +263,14 @@ ATARI_API int atari_env_launch_shape(atari_env *env, int *envs_per_warp, int *en
 ATARI_API int atari_env_info(atari_env *env, int *n_envs, size_t *device_bytes);
 
 /* Device bytes atari_env_create would allocate for this configuration
- * (used for admission against a memory budget). */
+ * (used for admission against a memory budget; Section 4 discusses the
+ * device-memory cost per environment of frames and emulator state). */
 ATARI_API size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg);
 
-/* Free everything; safe on NULL. */
+/* Free every device and host allocation of the env (library-owned state,
+ * logs, cache, ROM copies, captured graphs).  The paper defines no teardown;
+ * the caller must not use the env afterwards, and work still queued on a
+ * stream that uses it must have finished.  Safe on NULL. */
 ATARI_API void atari_env_destroy(atari_env *env);
 
 /*
@@ -273,7 +303,10 @@ ATARI_API int atari_step_noalloc(const uint8_t *rom, size_t rom_size, atari_rom_
                                  int32_t *d_rewards, uint8_t *d_dones, int n_envs, int frameskip, int sticky,
                                  uint64_t seed, atari_stream stream);
 
-/* Thread-local message describing the last error on this thread ("" if none). */
+/* Thread-local message describing the last failing call on this thread ("" if
+ * none).  Owned by the library; valid until the next call on the same
+ * thread.  The paper defines no error reporting; every entry point returns
+ * a negative ATARI_E* code and sets this message instead of throwing. */
 ATARI_API const char *atari_last_error(void);
 
 #ifdef __cplusplus

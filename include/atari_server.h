@@ -4,7 +4,7 @@
  * Many clients step their own sessions (n envs of one cartridge each) through
  * one GPU.  All machine state stays resident in device memory.  New sessions
  * are admitted while the device bytes they need fit a stated budget.  This
- * follows the paper's memory-limit discussion in Section 5 (frames and state
+ * follows the paper's memory-limit discussion in Section 4 (frames and state
  * grow linearly with the env count).  Step requests that arrive while earlier
  * ticks run on the GPU go into the next tick: continuous batching with up to
  * `inflight` ticks on the device at once, each on its own stream.  A tick
