@@ -63,6 +63,11 @@
  *       Taylor polynomial, and the action is the smallest j whose running
  *       sum exceeds u * total, u = (x >> 8) 2^-24 for the env's Philox word
  *       x (the last action with nonzero weight if rounding leaves none).
+ *   Learner-side targets over a rollout (Appendix, "A2C" and "V-trace"): the
+ *       bootstrapped N-step return of the A2C cost and the V-trace target of
+ *       its sum definition with truncated importance weights, in double
+ *       precision; a done inside the rollout ends the return (the discount
+ *       after a done step is 0), which the paper does not discuss.
  */
 #include "oracle.h"
 #include <math.h>
@@ -1307,4 +1312,85 @@ void orc_envs_policy(const orc_envs *e, const uint8_t *obs, const uint16_t *w, u
                                (int)((int64_t)e->n_envs * (t + 1) / n_threads)};
     for (int t = 0; t < n_threads; t++) pthread_create(&th[t], NULL, policy_worker, &jobs[t]);
     for (int t = 0; t < n_threads; t++) pthread_join(th[t], NULL);
+}
+
+/* Behaviour probability mu(a|s) of the sampled action (the quantity a
+ * training buffer keeps for V-trace, Appendix "V-trace"): the action's
+ * softmax weight over the total, the weights and total formed exactly as in
+ * orc_policy_sample, fp32 division. */
+float orc_policy_prob(const float *l, int a) {
+    float m = l[0];
+    for (int j = 1; j < ORC_POLICY_A; j++) if (l[j] > m) m = l[j];
+    float e[ORC_POLICY_A], tot = 0.0f;
+    for (int j = 0; j < ORC_POLICY_A; j++) { e[j] = orc_exp_own(l[j] - m); tot = tot + e[j]; }
+    return e[a] / tot;
+}
+
+void orc_envs_policy_mu(int n, const float *logits, const uint8_t *actions, float *mu) {
+    for (int i = 0; i < n; i++) mu[i] = orc_policy_prob(logits + (size_t)i * ORC_POLICY_A, actions[i]);
+}
+
+/* ------------------------------------------------------------------ learner-side targets
+ * Appendix, "A2C" and "V-trace": over a rollout of T steps of n envs,
+ * time-major arrays ([T][n]; values [T+1][n], row T the bootstrap value of
+ * the state after the last step), in double precision, each target written
+ * out as its sum definition.  Reading (the paper does not treat episode
+ * ends inside a rollout): a done at step t ends the return there, i.e. the
+ * discount after step t is gamma_t = gamma * (1 - done_t). */
+
+/* Bootstrapped N-step return of Eq. costPi:
+ *   R_t = sum_{i=0}^{k-1} gamma^i r_{t+i} + gamma^k V(s_{t+k}),  k = T - t,
+ * with the sum cut after the first done at or after t (no bootstrap then). */
+void orc_nstep_returns(int T, int n, const float *rewards, const uint8_t *dones, const float *values,
+                       double gamma, double *returns) {
+    for (int e = 0; e < n; e++) {
+        for (int t = 0; t < T; t++) {
+            double sum = 0.0, disc = 1.0;
+            int ended = 0;
+            for (int u = t; u < T; u++) {
+                sum += disc * (double)rewards[(size_t)u * n + e];
+                if (dones[(size_t)u * n + e]) { ended = 1; break; }
+                disc *= gamma;
+            }
+            if (!ended) sum += disc * (double)values[(size_t)T * n + e];
+            returns[(size_t)t * n + e] = sum;
+        }
+    }
+}
+
+/* V-trace target of Eq. target.off with the truncated importance weights of
+ * Eqs. rho and c:
+ *   v_t = V(s_t) + sum_{u=t}^{T-1} ( prod_{i=t}^{u-1} gamma_i c_i ) delta_u,
+ *   delta_u = rho_u ( r_u + gamma_u V(s_{u+1}) - V(s_u) ),
+ *   rho_u = min(rho_bar, pi_u / mu_u),  c_u = min(c_bar, pi_u / mu_u),
+ * (gamma_i in place of the constant gamma per the reading above), and the
+ * policy-gradient advantage of the paper's actor update,
+ *   A_t = rho_t ( r_t + gamma_t v_{t+1} - V(s_t) ),  v_T = V(s_T).
+ * pi and mu are the target and behaviour probabilities of the actions taken. */
+void orc_vtrace(int T, int n, const float *rewards, const uint8_t *dones, const float *values, const float *pi,
+                const float *mu, double gamma, double rho_bar, double c_bar, double *vs, double *pg_adv) {
+    for (int e = 0; e < n; e++) {
+        for (int t = 0; t < T; t++) {
+            double v = (double)values[(size_t)t * n + e], coef = 1.0;
+            for (int u = t; u < T; u++) {
+                const size_t k = (size_t)u * n + e;
+                const double g = dones[k] ? 0.0 : gamma;
+                const double ratio = (double)pi[k] / (double)mu[k];
+                const double rho = ratio < rho_bar ? ratio : rho_bar;
+                const double c = ratio < c_bar ? ratio : c_bar;
+                const double delta = rho * ((double)rewards[k] + g * (double)values[k + n] - (double)values[k]);
+                v += coef * delta;
+                coef *= g * c;
+            }
+            vs[(size_t)t * n + e] = v;
+        }
+        for (int t = 0; t < T; t++) {
+            const size_t k = (size_t)t * n + e;
+            const double g = dones[k] ? 0.0 : gamma;
+            const double ratio = (double)pi[k] / (double)mu[k];
+            const double rho = ratio < rho_bar ? ratio : rho_bar;
+            const double vnext = t + 1 < T ? vs[k + n] : (double)values[(size_t)T * n + e];
+            pg_adv[k] = rho * ((double)rewards[k] + g * vnext - (double)values[k]);
+        }
+    }
 }

@@ -108,6 +108,20 @@ int orc_policy_sample(const float *logits18, uint32_t u);
 void orc_envs_policy(const orc_envs *e, const uint8_t *obs, const uint16_t *w_bf16, uint8_t *actions,
                      float *logits, int n_threads);
 
+/* behaviour probability of action a under the softmax of logits18 (fp32,
+ * weights and total as in orc_policy_sample) */
+float orc_policy_prob(const float *logits18, int a);
+/* mu[i] = orc_policy_prob(logits[i], actions[i]) for n envs */
+void orc_envs_policy_mu(int n, const float *logits, const uint8_t *actions, float *mu);
+
+/* ---- learner-side targets over a rollout (Appendix: A2C, V-trace) ----
+ * Time-major [T][n] arrays; values [T+1][n] (row T: bootstrap value);
+ * double-precision outputs [T][n]; a done at step t ends the return there. */
+void orc_nstep_returns(int T, int n, const float *rewards, const uint8_t *dones, const float *values,
+                       double gamma, double *returns);
+void orc_vtrace(int T, int n, const float *rewards, const uint8_t *dones, const float *values, const float *pi,
+                const float *mu, double gamma, double rho_bar, double c_bar, double *vs, double *pg_adv);
+
 /* ---- preprocessing of one env-step (exposed for the downsample pins) ---- */
 void orc_preprocess(const uint8_t *f3, const uint8_t *f4, const uint8_t *luma128,
                     uint8_t *out84x84);

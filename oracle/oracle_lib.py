@@ -81,6 +81,11 @@ def lib():
             L.orc_policy_logits.argtypes = [P, P, P]
             L.orc_policy_sample.argtypes = [P, C.c_uint32]
             L.orc_envs_policy.argtypes = [P, P, P, P, P, C.c_int]
+            L.orc_policy_prob.argtypes = [P, C.c_int]
+            L.orc_policy_prob.restype = C.c_float
+            L.orc_envs_policy_mu.argtypes = [C.c_int, P, P, P]
+            L.orc_nstep_returns.argtypes = [C.c_int, C.c_int, P, P, P, C.c_double, P]
+            L.orc_vtrace.argtypes = [C.c_int, C.c_int, P, P, P, P, P, C.c_double, C.c_double, C.c_double, P, P]
             _lib = L
     return _lib
 
@@ -124,6 +129,49 @@ def policy_logits(stack: np.ndarray, w_bf16: np.ndarray) -> np.ndarray:
 def policy_sample(logits: np.ndarray, u: int) -> int:
     l = np.ascontiguousarray(logits, dtype=np.float32)
     return lib().orc_policy_sample(_ptr(l), u)
+
+
+def policy_prob(logits: np.ndarray, a: int) -> float:
+    l = np.ascontiguousarray(logits, dtype=np.float32)
+    return lib().orc_policy_prob(_ptr(l), int(a))
+
+
+def policy_mu(logits: np.ndarray, actions: np.ndarray) -> np.ndarray:
+    """Behaviour probability of each env's sampled action, fp32 [n]."""
+    l = np.ascontiguousarray(logits, dtype=np.float32).reshape(-1, 18)
+    a = np.ascontiguousarray(actions, dtype=np.uint8)
+    mu = np.zeros(l.shape[0], dtype=np.float32)
+    lib().orc_envs_policy_mu(l.shape[0], _ptr(l), _ptr(a), _ptr(mu))
+    return mu
+
+
+def _rollout_args(rewards, dones, values):
+    r = np.ascontiguousarray(rewards, dtype=np.float32)
+    d = np.ascontiguousarray(dones, dtype=np.uint8)
+    v = np.ascontiguousarray(values, dtype=np.float32)
+    T, n = r.shape
+    assert d.shape == (T, n) and v.shape == (T + 1, n)
+    return r, d, v, T, n
+
+
+def nstep_returns(rewards, dones, values, gamma: float) -> np.ndarray:
+    """Bootstrapped N-step returns [T][n] (float64) of a time-major rollout."""
+    r, d, v, T, n = _rollout_args(rewards, dones, values)
+    out = np.zeros((T, n), dtype=np.float64)
+    lib().orc_nstep_returns(T, n, _ptr(r), _ptr(d), _ptr(v), gamma, _ptr(out))
+    return out
+
+
+def vtrace(rewards, dones, values, pi, mu, gamma: float, rho_bar: float, c_bar: float):
+    """V-trace targets and policy-gradient advantages [T][n] (float64)."""
+    r, d, v, T, n = _rollout_args(rewards, dones, values)
+    p = np.ascontiguousarray(pi, dtype=np.float32)
+    m = np.ascontiguousarray(mu, dtype=np.float32)
+    assert p.shape == (T, n) and m.shape == (T, n)
+    vs = np.zeros((T, n), dtype=np.float64)
+    adv = np.zeros((T, n), dtype=np.float64)
+    lib().orc_vtrace(T, n, _ptr(r), _ptr(d), _ptr(v), _ptr(p), _ptr(m), gamma, rho_bar, c_bar, _ptr(vs), _ptr(adv))
+    return vs, adv
 
 
 def preprocess(f3: np.ndarray, f4: np.ndarray, luma: bytes) -> np.ndarray:
