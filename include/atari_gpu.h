@@ -90,6 +90,10 @@ typedef struct {
                              CPU warp takes the TIA writes, logging and collisions off the CPU's
                              path; 0 = autotune; 3 = as 2 with the TIA side switched off, to test the
                              bounded waits (every env ends its steps with ATARI_ST_STALL) */
+    int grouping;         /* batched form, how envs of one cartridge are ordered into warps: 1 = env order;
+                             2 = bank-aware: re-sorted at every step by the bank their state holds at the
+                             step's start (stable in env order), so a warp's lanes start in one bank of an
+                             F8/F6 cartridge; 0 = autotune */
 } atari_config;
 
 /* Fill *cfg with the paper's defaults: F = 4, no sticky actions, 30 cached
@@ -182,6 +186,52 @@ ATARI_API int atari_env_rollout(atari_env *env, const uint16_t *d_weights, int n
                                 uint8_t *d_actions, int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes,
                                 float *d_ring_rewards, int ring_depth, int ring_start, atari_stream stream);
 
+/*
+ * The inference-path loop with the training buffer V-trace needs (paper
+ * Appendix, "V-trace": the behaviour probabilities mu(a|s) are stored with
+ * the experiences).  As atari_env_rollout, and also: d_ring_dones (device,
+ * uint8 [ring_depth][n], may be NULL) receives each step's dones, d_ring_mu
+ * (device, float [ring_depth][n], may be NULL) the probability the policy
+ * gave the action it sampled (its softmax weight over the total, fp32), in
+ * the same ring slot as the step's plane and reward.
+ */
+ATARI_API int atari_env_rollout_ex(atari_env *env, const uint16_t *d_weights, int n_steps, uint8_t *d_obs,
+                                   uint8_t *d_actions, int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes,
+                                   float *d_ring_rewards, uint8_t *d_ring_dones, float *d_ring_mu, int ring_depth,
+                                   int ring_start, atari_stream stream);
+
+/*
+ * Learner-side targets over a rollout held in a device ring (paper Appendix,
+ * "A2C": the bootstrapped N-step return R_t = sum_{i<k} gamma^i r_{t+i} +
+ * gamma^k V(s_{t+k}); "V-trace": the target v_t of the sum definition with
+ * truncated importance weights rho_t = min(rho_bar, pi_t / mu_t) and c_t =
+ * min(c_bar, pi_t / mu_t), computed by the paper's recursive form
+ * v_t = V_t + delta_t + gamma c_t (v_{t+1} - V_{t+1}), and the actor's
+ * advantage rho_t (r_t + gamma v_{t+1} - V_t)).
+ *
+ * Step t (0 <= t < T) of the rollout is ring slot (ring_start + t) mod
+ * ring_depth of d_rewards (float [ring_depth][n]), d_dones (uint8, same
+ * shape) and d_mu (float, same shape: behaviour probabilities, > 0), as
+ * atari_env_rollout_ex writes them.  d_values (float [T + 1][n]) holds
+ * V(s_0) .. V(s_T), row T the bootstrap value of the state after the last
+ * step; d_pi (float [T][n]) the target policy's probabilities of the actions
+ * taken.  Outputs (float [T][n], time-major): d_returns; d_vs (targets) and
+ * d_pg_adv (advantages).  All buffers are device memory owned by the caller.
+ * Reading where the paper is silent: a done at step t ends the return there
+ * (the discount after step t is 0, no bootstrap across an episode end).
+ * fp32, one rounding per operation in the order above, so results are
+ * within a few units of fp32 rounding of the exact values, not bit-equal to
+ * a double computation.  ATARI_EINVAL for T < 1, T > ring_depth,
+ * ring_start < 0, gamma outside [0, 1], rho_bar < c_bar or c_bar < 0, or a
+ * NULL buffer with n > 0.  Enqueued on `stream`.
+ */
+ATARI_API int atari_nstep_returns(const float *d_rewards, const uint8_t *d_dones, int ring_depth, int ring_start,
+                                  const float *d_values, int T, int n, float gamma, float *d_returns,
+                                  atari_stream stream);
+ATARI_API int atari_vtrace(const float *d_rewards, const uint8_t *d_dones, const float *d_mu, int ring_depth,
+                           int ring_start, const float *d_values, const float *d_pi, int T, int n, float gamma,
+                           float rho_bar, float c_bar, float *d_vs, float *d_pg_adv, atari_stream stream);
+
 /* d_status (device, uint32 [n]) <- per-env status bits (ATARI_ST_*), on
  * `stream`.  The paper is silent on machine faults; here they never fail a
  * call: an undocumented opcode halts that env's CPU (done at step end), a
@@ -231,9 +281,15 @@ ATARI_API int atari_env_get_frames(atari_env *env, uint8_t *d_dst, atari_stream 
  * Device buffer owned by the caller, copied on `stream`. */
 ATARI_API int atari_env_get_cache(atari_env *env, void *d_dst, atari_stream stream);
 
-/* Counters of the last step: 6502 instructions retired (sum over envs) and
- * TIA log records written.  Host pointers; synchronises `stream`. */
-ATARI_API int atari_env_counters(atari_env *env, uint64_t *instructions, uint64_t *log_records, atari_stream stream);
+/* Counters of the last step: 6502 instructions retired (sum over envs), TIA
+ * log records written, and lockstep issue rounds summed over the envs (each
+ * env counts the rounds its warp issued, so instructions / lane_rounds is
+ * the fraction of a warp's lanes that execute per round: the emulated-
+ * instruction SIMT efficiency the paper's divergence discussion in Section 4
+ * is about; 0 in the plain form, which has no lockstep issue).  Host
+ * pointers, any may be NULL; synchronises `stream`. */
+ATARI_API int atari_env_counters(atari_env *env, uint64_t *instructions, uint64_t *log_records,
+                                 uint64_t *lane_rounds, atari_stream stream);
 
 /*
  * Per-kernel device timing.  With profiling enabled, every kernel launch of
@@ -249,15 +305,19 @@ ATARI_API int atari_env_counters(atari_env *env, uint64_t *instructions, uint64_
 #define ATARI_PROF_FUSED 3      /* fused replay + preprocessing (batched form) */
 #define ATARI_PROF_COPY 4       /* output copies, rollout-ring appends */
 #define ATARI_PROF_POLICY 5     /* linear softmax policy */
+#define ATARI_PROF_GROUP 6      /* bank-aware regrouping of the env list (batched form, grouping 2) */
 ATARI_API int atari_env_profile(atari_env *env, int enable);
 ATARI_API int atari_env_profile_read(atari_env *env, double *ms, uint64_t *launches);
 
 /* Launch shape in use (batched form: the autotuned or configured values;
  * plain form: 32 envs per warp, 128 per block, 1 warp per frame, and the
  * grid of the interpreter launch).  tia_warps: 2 when paired TIA warps run
- * the envs' TIA side, else 1.  Host pointers; any may be NULL. */
+ * the envs' TIA side, else 1.  grouping: 1 env order, 2 bank-aware (see
+ * atari_config; the plain form reports 1).  Host pointers; any may be NULL.
+ * The paper runs one emulator per thread with no grouping (Section 3); the
+ * shape is this library's own tuning and changes speed only, never results. */
 ATARI_API int atari_env_launch_shape(atari_env *env, int *envs_per_warp, int *envs_per_block,
-                                     int *raster_warps_per_frame, int *grid, int *tia_warps);
+                                     int *raster_warps_per_frame, int *grid, int *tia_warps, int *grouping);
 
 /* Number of envs, and the bytes of device memory the env holds. */
 ATARI_API int atari_env_info(atari_env *env, int *n_envs, size_t *device_bytes);
@@ -288,7 +348,9 @@ ATARI_API void atari_env_destroy(atari_env *env);
  * atari_env_step.  d_frame (device, n*210*160, may be NULL) receives frame F
  * (palette values), d_rewards / d_dones (device, may be NULL) the rewards and
  * dones.  Results equal atari_env_step of a plain-form env with palette
- * output on the same states and actions.
+ * output and log_cap 4096 on the same states and actions: the scratch log
+ * holds 4096 TIA writes per rendered frame, so a frame with more writes is
+ * truncated and its env flagged ATARI_ST_LOG_OVERFLOW, as in such an env.
  *
  * Its scratch (the cartridge image, TIA-write logs and frame records) is one
  * fixed array of about 2.1 MB inside the library, held by every GPU that

@@ -4,6 +4,7 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -31,6 +32,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if all(os.path.getmtime(d) <= t for d in DEPS if os.path.exists(d)):
             return LIB
     tmp = LIB + f".tmp{os.getpid()}"
+    t_start = time.time()
     flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
              "--expt-relaxed-constexpr"]
     if verbose:
@@ -61,6 +63,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed building libatari_gpu.so")
     os.replace(tmp, LIB)
+    # stamp the library with the time the build started, so a source edited
+    # while it compiled makes it stale
+    os.utime(LIB, (t_start, t_start))
     return LIB
 
 

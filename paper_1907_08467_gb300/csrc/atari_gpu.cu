@@ -22,6 +22,7 @@
 #include "render.cuh"
 #include "batched.cuh"
 #include "policy.cuh"
+#include "learner.cuh"
 
 using namespace atari;
 
@@ -100,9 +101,11 @@ uint32_t cycles_for(uint32_t op, uint32_t mode, bool &penalty) {
   }
 }
 
-std::vector<uint32_t> build_decode_table() {
-  std::vector<uint32_t> t(256, 0u);
+// t[256] <- per opcode: operation | mode << 8 | base cycles << 12 | page-cross
+// penalty << 15; 0 for undocumented opcodes.
+void fill_decode_table(uint32_t *t) {
   for (int o = 0; o < 256; ++o) {
+    t[o] = 0;
     if (!OPMAP[o]) continue;
     char mn[4] = {OPMAP[o][0], OPMAP[o][1], OPMAP[o][2], 0};
     const char *md = OPMAP[o] + 4;
@@ -115,7 +118,21 @@ std::vector<uint32_t> build_decode_table() {
     uint32_t cyc = cycles_for(op, mode, pen);
     t[o] = op | mode << 8 | cyc << 12 | (pen ? 1u : 0u) << 15;
   }
+}
+
+std::vector<uint32_t> build_decode_table() {
+  std::vector<uint32_t> t(256, 0u);
+  fill_decode_table(t.data());
   return t;
+}
+
+int scheme_of(size_t sz);
+
+// Cartridge info word: scheme | score RAM index << 8 | game-over RAM index
+// << 16 | 4 KB banks << 24 (a 2 KB image counts as one bank).
+uint32_t rom_info_word(size_t rom_size, const atari_rom_meta &meta) {
+  return (uint32_t)scheme_of(rom_size) | (uint32_t)(meta.score_addr & 0x7F) << 8 |
+         (uint32_t)(meta.gameover_addr & 0x7F) << 16 | (uint32_t)(rom_size <= 4096 ? 1u : rom_size / 4096) << 24;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -292,8 +309,9 @@ __device__ void step_env(Console<Mem> &m, uint8_t *st, int i, const StepArgs &a,
   if (a.rew_out) a.rew_out[i] = reward;
   if (a.done_out) a.done_out[i] = (uint8_t)done;
   if (a.counters) {
-    a.counters[2 * i] = m.instret;
-    a.counters[2 * i + 1] = log_total;
+    a.counters[3 * i] = m.instret;
+    a.counters[3 * i + 1] = log_total;
+    a.counters[3 * i + 2] = 0;  // one thread per env: no lockstep issue rounds
   }
   Console<Mem>::st32(st + S::STATUS, env_status);
   Console<Mem>::st32(st + S::STEP, step_no + 1);
@@ -466,6 +484,10 @@ struct atari_env {
   uint8_t *d_romb = nullptr;        // [n_roms][16384] cartridge bytes for the batched stage
   uint8_t *d_dec_op = nullptr;      // 512 bytes
   int32_t *d_grp = nullptr;         // rom, start, count per work item (3 * n_groups) then perm (n)
+  int32_t *d_seg = nullptr;         // first env-list position of each cartridge (n_roms + 1)
+  int32_t *d_perm_dyn = nullptr;    // bank-aware grouping: the env list re-sorted at every step
+  int grouping = 1;                 // 1 env order, 2 bank-aware
+  bool banked = false;              // some cartridge has more than one bank
   int *d_queue = nullptr;
   int n_groups = 0, lanes = 32, warps = 4, wpf = 4, grid = 0, rom_stage = 4096, max_blocks = 1;
   bool split = false;   // paired CPU / TIA warps (k_interp_split)
@@ -503,9 +525,10 @@ int validate(const atari_config &c) {
   if (c.log_cap < 256 || c.log_cap > (1 << 20)) return fail(ATARI_EINVAL, "log_cap must be in 256..2^20");
   if (c.sticky != 0 && c.sticky != 1) return fail(ATARI_EINVAL, "sticky must be 0 or 1");
   if (c.envs_per_block < 0 || c.envs_per_block > 128 || c.envs_per_warp < 0 || c.envs_per_warp > 32 ||
-      c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4 || c.tia_warps < 0 || c.tia_warps > 3)
+      c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4 || c.tia_warps < 0 || c.tia_warps > 3 ||
+      c.grouping < 0 || c.grouping > 2)
     return fail(ATARI_EINVAL, "envs_per_block must be 0..128, envs_per_warp 0..32, raster_warps_per_frame 0..4, "
-                              "tia_warps 0..3");
+                              "tia_warps 0..3, grouping 0..2");
   return 0;
 }
 
@@ -531,6 +554,15 @@ int build_groups(atari_env *E, int lanes, int warps, bool split) {
     }
   }
   const int ng = (int)rom.size();
+  if (E->d_seg) {
+    std::vector<int32_t> seg(E->n_roms + 1, 0);
+    for (int r = 0, p = 0; r < E->n_roms; ++r) {
+      seg[r] = p;
+      for (int i = 0; i < E->n; ++i) p += E->h_env_rom[i] == r ? 1 : 0;
+      seg[r + 1] = p;
+    }
+    CUDA_TRY(cudaMemcpy(E->d_seg, seg.data(), seg.size() * 4, cudaMemcpyHostToDevice));
+  }
   std::vector<int32_t> blob;
   blob.insert(blob.end(), rom.begin(), rom.end());
   blob.insert(blob.end(), start.begin(), start.end());
@@ -584,7 +616,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
   a.grp_rom = E->d_grp;
   a.grp_start = E->d_grp + E->n_groups;
   a.grp_count = E->d_grp + 2 * E->n_groups;
-  a.perm = E->d_grp + 3 * E->n_groups;
+  a.perm = E->grouping == 2 ? E->d_perm_dyn : E->d_grp + 3 * E->n_groups;
   a.opos = nullptr;
   a.queue = E->d_queue;
   a.n_groups = E->n_groups;
@@ -611,6 +643,13 @@ void launch_interp(atari_env *E, const BatchArgs &a, int grid, cudaStream_t s) {
 }
 
 size_t fused_smem() { return 2 * 210 * 160 + 128 + 7056; }
+
+// Bank-aware grouping: the env list of this step, re-sorted by bank within
+// each cartridge from the states as they stand.
+void launch_regroup(atari_env *E, cudaStream_t s) {
+  k_group_by_bank<<<E->n_roms, 256, 0, s>>>(E->d_state, E->d_grp + 3 * E->n_groups, E->d_seg, E->d_info,
+                                             E->d_perm_dyn);
+}
 
 struct ProfScope;  // defined below
 int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vector<uint32_t> &dec);
@@ -680,10 +719,10 @@ size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg) {
   b += n * 2 * (size_t)cfg->log_cap * 4;                  // log
   b += n * 2 * 64 + n * 2 * 2 * 4;                        // snapshots, meta
   if (cfg->form == ATARI_FORM_PLAIN) b += n * 2 * 210 * 160;   // frames (plain form only)
-  else b += (size_t)n_roms * 16384 + 512 + n * 4 + 64;         // cartridge bytes for the stage, work items
+  else b += (size_t)n_roms * 16384 + 512 + n * 8 + 64 + (size_t)(n_roms + 1) * 4;  // stage bytes, work items, regrouping
   if (cfg->output_mode == ATARI_OUT_STACK) b += n * 4 * 7056 + n;
   if (cfg->output_mode == ATARI_OUT_STACK && cfg->form == ATARI_FORM_BATCHED) b += n * 2 * 3 * 64;  // band snapshots
-  b += n * (4 + 1 + 8 + 1);                               // rewards, dones, counters, action staging
+  b += n * (4 + 1 + 12 + 1);                              // rewards, dones, counters, action staging
   return b;
 }
 
@@ -727,7 +766,7 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
       (rc = dalloc(&E->d_log, n * 2 * (size_t)c.log_cap * 4, T)) || (rc = dalloc(&E->d_snap, n * 2 * 64, T)) ||
       (rc = dalloc(&E->d_meta, n * 2 * 2 * 4, T)) ||
       (c.form == ATARI_FORM_PLAIN && (rc = dalloc(&E->d_frames, n * 2 * 210 * 160, T))) ||
-      (rc = dalloc(&E->d_rew, n * 4, T)) || (rc = dalloc(&E->d_done, n, T)) || (rc = dalloc(&E->d_ctr, n * 8, T)) ||
+      (rc = dalloc(&E->d_rew, n * 4, T)) || (rc = dalloc(&E->d_done, n, T)) || (rc = dalloc(&E->d_ctr, n * 12, T)) ||
       (rc = dalloc(&E->d_act, n, T)) || (rc = dalloc(&E->d_luma, 128, T)))
     return bail(rc);
   if (c.output_mode == ATARI_OUT_STACK) {
@@ -751,9 +790,7 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
     } else {
       memcpy(dst, roms[r], rom_sizes[r]);
     }
-    info[r] = (uint32_t)scheme_of(rom_sizes[r]) | (uint32_t)(meta[r].score_addr & 0x7F) << 8 |
-              (uint32_t)(meta[r].gameover_addr & 0x7F) << 16 |
-              (uint32_t)(rom_sizes[r] <= 4096 ? 1u : rom_sizes[r] / 4096) << 24;
+    info[r] = rom_info_word(rom_sizes[r], meta[r]);
     // power-on state: registers and RAM zero, SP $FD, P $24, PC from the reset
     // vector of bank 0, timer 0 with interval 1024 written at cycle 0
     uint8_t *p = power.data() + (size_t)r * 256;
@@ -817,7 +854,8 @@ void atari_env_destroy(atari_env *E) {
   if (!E) return;
   void *ptrs[] = {E->d_roms, E->d_info, E->d_dec, E->d_env_rom, E->d_env_key, E->d_state, E->d_cache, E->d_log,
                   E->d_snap, E->d_bsnap, E->d_meta, E->d_frames, E->d_ring, E->d_head, E->d_luma, E->d_rew, E->d_done,
-                  E->d_ctr, E->d_act, E->d_obs_tmp, E->d_romb, E->d_dec_op, E->d_grp, E->d_queue};
+                  E->d_ctr, E->d_act, E->d_obs_tmp, E->d_romb, E->d_dec_op, E->d_grp, E->d_queue, E->d_seg,
+                  E->d_perm_dyn};
   for (auto &g : E->graphs) cudaGraphExecDestroy(g.exec);
   if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
   for (void *p : ptrs)
@@ -902,6 +940,10 @@ int launch_batched(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
                    cudaStream_t s) {
   const atari_config &c = E->cfg;
   BatchArgs a = batch_args(E, d_actions, d_rewards, d_dones);
+  if (E->grouping == 2) {
+    ProfScope p(E, ATARI_PROF_GROUP, s);
+    launch_regroup(E, s);
+  }
   CUDA_TRY(cudaMemsetAsync(E->d_queue, 0, sizeof(int), s));
   {
     ProfScope p(E, ATARI_PROF_INTERP, s);
@@ -972,7 +1014,8 @@ int autotune(atari_env *E) {
   // (envs per warp, CPU warps per block, paired TIA warps)
   const int cand[][3] = {{32, 4, 0}, {32, 2, 0}, {32, 1, 0}, {16, 4, 0}, {16, 2, 0}, {16, 1, 0}, {8, 4, 0},
                          {8, 2, 0},  {8, 1, 0},  {4, 4, 0},  {4, 2, 0},  {4, 1, 0},  {2, 4, 0},  {2, 2, 0},
-                         {1, 4, 0},  {32, 4, 1}, {32, 2, 1}, {32, 1, 1}, {16, 4, 1}, {16, 2, 1}};
+                         {1, 4, 0},  {32, 4, 1}, {32, 2, 1}, {32, 1, 1}, {16, 4, 1}, {16, 2, 1}, {16, 1, 1},
+                         {8, 4, 1},  {8, 2, 1},  {8, 1, 1}};
   // shapes within 3 % of the fastest count as equal; the first of them in
   // candidate order (the widest warps) is taken, so the choice is stable
   // from run to run
@@ -1004,6 +1047,31 @@ int autotune(atari_env *E) {
   for (auto &p : timed)
     if (p.first <= 1.03f * best) { bl = cand[p.second][0]; bw = cand[p.second][1]; bs = cand[p.second][2]; break; }
   int rc = build_groups(E, bl, bw, bs != 0);
+  // ROM-to-warp grouping on the chosen shape: env order, or bank-aware
+  // (the regrouping kernel's time counted with the interpreter's); the
+  // bank-aware order must be 3 % faster to be taken
+  E->grouping = E->cfg.grouping ? E->cfg.grouping : 1;
+  if (!rc && E->cfg.grouping == 0 && E->banked) {
+    float tg[3] = {0, 0, 0};
+    for (int g = 1; g <= 2 && !rc; ++g) {
+      E->grouping = g;
+      BatchArgs a = batch_args(E, E->d_act, nullptr, nullptr);
+      for (int rep = 0; rep < 2; ++rep) {
+        if (cudaMemcpy(E->d_state, st_bak, n * 256, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemset(E->d_queue, 0, sizeof(int)) != cudaSuccess) {
+          rc = fail(ATARI_ECUDA, "autotune: state restore failed");
+          break;
+        }
+        cudaEventRecord(e0);
+        if (g == 2) launch_regroup(E, nullptr);
+        launch_interp(E, a, E->grid, nullptr);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&tg[g], e0, e1);
+      }
+    }
+    E->grouping = tg[2] < 0.97f * tg[1] ? 2 : 1;
+  }
   if (!rc && E->cfg.output_mode == ATARI_OUT_STACK) {
     if (!(rc = dalloc(&ring_bak, n * 4 * 7056, dummy)) && !(rc = dalloc(&head_bak, n, dummy))) {
       cudaMemcpy(ring_bak, E->d_ring, n * 4 * 7056, cudaMemcpyDeviceToDevice);
@@ -1057,7 +1125,10 @@ int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vect
     memcpy(bytes.data() + (size_t)r * 16384, img.data() + (size_t)r * ROM_SLOT, (size_t)banks * 4096);
   }
   E->rom_stage = (int)max_banks * 4096;
+  E->banked = max_banks > 1;
   size_t &T = E->bytes;
+  if (int rc = dalloc(&E->d_seg, (size_t)(R + 1) * 4, T)) return rc;
+  if (int rc = dalloc(&E->d_perm_dyn, std::max<size_t>((size_t)E->n, 1) * 4, T)) return rc;
   if (int rc = dalloc(&E->d_romb, bytes.size(), T)) return rc;
   if (int rc = dalloc(&E->d_dec_op, 512, T)) return rc;
   if (int rc = dalloc(&E->d_queue, 64, T)) return rc;
@@ -1069,8 +1140,10 @@ int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vect
   if (c.envs_per_block > 0 && c.envs_per_warp > 0) {
     int L = std::min(32, c.envs_per_warp), W = std::max(1, std::min(4, c.envs_per_block / L));
     E->wpf = c.raster_warps_per_frame > 0 ? c.raster_warps_per_frame : 4;
+    E->grouping = c.grouping ? c.grouping : 1;
     return build_groups(E, L, W, c.tia_warps >= 2);
   }
+  E->grouping = c.grouping ? c.grouping : 1;
   if (E->n == 0) return build_groups(E, 32, 4, c.tia_warps >= 2);
   return autotune(E);
 }
@@ -1156,18 +1229,20 @@ int atari_env_get_cache(atari_env *E, void *d_dst, atari_stream stream) {
   return 0;
 }
 
-int atari_env_counters(atari_env *E, uint64_t *instructions, uint64_t *log_records, atari_stream stream) {
+int atari_env_counters(atari_env *E, uint64_t *instructions, uint64_t *log_records, uint64_t *lane_rounds,
+                       atari_stream stream) {
   g_err.clear();
   if (!E) return fail(ATARI_EINVAL, "env is NULL");
-  std::vector<uint32_t> h((size_t)E->n * 2);
+  std::vector<uint32_t> h((size_t)E->n * 3);
   if (E->n) {
     CUDA_TRY(cudaMemcpyAsync(h.data(), E->d_ctr, h.size() * 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
   }
-  uint64_t a = 0, b = 0;
-  for (int i = 0; i < E->n; ++i) { a += h[2 * i]; b += h[2 * i + 1]; }
+  uint64_t a = 0, b = 0, c = 0;
+  for (int i = 0; i < E->n; ++i) { a += h[3 * i]; b += h[3 * i + 1]; c += h[3 * i + 2]; }
   if (instructions) *instructions = a;
   if (log_records) *log_records = b;
+  if (lane_rounds) *lane_rounds = c;
   return 0;
 }
 
@@ -1182,15 +1257,16 @@ int atari_env_policy(atari_env *E, const uint8_t *d_obs, const uint16_t *d_weigh
   {
     ProfScope p(E, ATARI_PROF_POLICY, s);
     k_policy<<<(E->n + POLICY_TPB - 1) / POLICY_TPB, POLICY_TPB, 0, s>>>(d_obs, d_weights, E->d_state, d_actions,
-                                                                      d_logits, E->n, E->cfg.seed);
+                                                                      d_logits, nullptr, E->n, E->cfg.seed);
   }
   CUDA_TRY(cudaGetLastError());
   return 0;
 }
 
-int atari_env_rollout(atari_env *E, const uint16_t *d_weights, int n_steps, uint8_t *d_obs, uint8_t *d_actions,
-                      int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes, float *d_ring_rewards,
-                      int ring_depth, int ring_start, atari_stream stream) {
+int atari_env_rollout_ex(atari_env *E, const uint16_t *d_weights, int n_steps, uint8_t *d_obs, uint8_t *d_actions,
+                         int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes, float *d_ring_rewards,
+                         uint8_t *d_ring_dones, float *d_ring_mu, int ring_depth, int ring_start,
+                         atari_stream stream) {
   g_err.clear();
   if (!E) return fail(ATARI_EINVAL, "env is NULL");
   if (E->cfg.output_mode != ATARI_OUT_STACK) return fail(ATARI_EINVAL, "the rollout loop needs stack output");
@@ -1200,15 +1276,65 @@ int atari_env_rollout(atari_env *E, const uint16_t *d_weights, int n_steps, uint
     return fail(ATARI_EINVAL, "NULL buffer");
   cudaStream_t s = (cudaStream_t)stream;
   for (int t = 0; t < n_steps; ++t) {
-    if (int rc = atari_env_policy(E, d_obs, d_weights, d_actions, nullptr, stream)) return rc;
+    const int slot = (int)(((long long)ring_start + t) % ring_depth);
+    {
+      ProfScope p(E, ATARI_PROF_POLICY, s);
+      k_policy<<<(E->n + POLICY_TPB - 1) / POLICY_TPB, POLICY_TPB, 0, s>>>(
+          d_obs, d_weights, E->d_state, d_actions, nullptr, d_ring_mu ? d_ring_mu + (size_t)slot * E->n : nullptr,
+          E->n, E->cfg.seed);
+    }
+    CUDA_TRY(cudaGetLastError());
     if (int rc = atari_env_step(E, d_actions, d_obs, d_rewards, d_dones, stream)) return rc;
     {
       ProfScope p(E, ATARI_PROF_COPY, s);
-      k_ring_append<<<E->n, 128, 0, s>>>(d_obs, d_rewards, d_ring_planes, d_ring_rewards, E->n,
-                                        (ring_start + t) % ring_depth);
+      k_ring_append<<<E->n, 128, 0, s>>>(d_obs, d_rewards, d_dones, d_ring_planes, d_ring_rewards, d_ring_dones,
+                                        E->n, slot);
     }
     CUDA_TRY(cudaGetLastError());
   }
+  return 0;
+}
+
+int atari_env_rollout(atari_env *E, const uint16_t *d_weights, int n_steps, uint8_t *d_obs, uint8_t *d_actions,
+                      int32_t *d_rewards, uint8_t *d_dones, uint8_t *d_ring_planes, float *d_ring_rewards,
+                      int ring_depth, int ring_start, atari_stream stream) {
+  return atari_env_rollout_ex(E, d_weights, n_steps, d_obs, d_actions, d_rewards, d_dones, d_ring_planes,
+                              d_ring_rewards, nullptr, nullptr, ring_depth, ring_start, stream);
+}
+
+static int check_rollout_args(const void *rew, const void *done, int depth, int start, const void *values, int T,
+                              int n, float gamma) {
+  if (n < 0 || T < 1 || depth < T || start < 0) return fail(ATARI_EINVAL, "need n >= 0, 1 <= T <= ring_depth, ring_start >= 0");
+  if (!(gamma >= 0.0f && gamma <= 1.0f)) return fail(ATARI_EINVAL, "gamma must be in [0, 1]");
+  if (n > 0 && (!rew || !done || !values)) return fail(ATARI_EINVAL, "NULL buffer");
+  return 0;
+}
+
+int atari_nstep_returns(const float *d_rewards, const uint8_t *d_dones, int ring_depth, int ring_start,
+                        const float *d_values, int T, int n, float gamma, float *d_returns, atari_stream stream) {
+  g_err.clear();
+  if (int rc = check_rollout_args(d_rewards, d_dones, ring_depth, ring_start, d_values, T, n, gamma)) return rc;
+  if (n == 0) return 0;
+  if (!d_returns) return fail(ATARI_EINVAL, "NULL buffer");
+  k_nstep_returns<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_rewards, d_dones, ring_depth,
+                                                                     ring_start % ring_depth, d_values, T, n, gamma,
+                                                                     d_returns);
+  CUDA_TRY(cudaGetLastError());
+  return 0;
+}
+
+int atari_vtrace(const float *d_rewards, const uint8_t *d_dones, const float *d_mu, int ring_depth, int ring_start,
+                 const float *d_values, const float *d_pi, int T, int n, float gamma, float rho_bar, float c_bar,
+                 float *d_vs, float *d_pg_adv, atari_stream stream) {
+  g_err.clear();
+  if (int rc = check_rollout_args(d_rewards, d_dones, ring_depth, ring_start, d_values, T, n, gamma)) return rc;
+  if (!(c_bar >= 0.0f && rho_bar >= c_bar)) return fail(ATARI_EINVAL, "need rho_bar >= c_bar >= 0");
+  if (n == 0) return 0;
+  if (!d_mu || !d_pi || !d_vs || !d_pg_adv) return fail(ATARI_EINVAL, "NULL buffer");
+  k_vtrace<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(d_rewards, d_dones, d_mu, ring_depth,
+                                                              ring_start % ring_depth, d_values, d_pi, T, n, gamma,
+                                                              rho_bar, c_bar, d_vs, d_pg_adv);
+  CUDA_TRY(cudaGetLastError());
   return 0;
 }
 
@@ -1237,7 +1363,7 @@ int atari_env_profile_read(atari_env *E, double *ms, uint64_t *launches) {
 }
 
 int atari_env_launch_shape(atari_env *E, int *envs_per_warp, int *envs_per_block, int *raster_warps_per_frame,
-                           int *grid, int *tia_warps) {
+                           int *grid, int *tia_warps, int *grouping) {
   g_err.clear();
   if (!E) return fail(ATARI_EINVAL, "env is NULL");
   const bool b = E->cfg.form == ATARI_FORM_BATCHED;
@@ -1246,6 +1372,7 @@ int atari_env_launch_shape(atari_env *E, int *envs_per_warp, int *envs_per_block
   if (raster_warps_per_frame) *raster_warps_per_frame = b ? E->wpf : 1;
   if (grid) *grid = b ? E->grid : (E->n + 127) / 128;
   if (tia_warps) *tia_warps = (b && E->split) ? 2 : 1;
+  if (grouping) *grouping = b ? E->grouping : 1;
   return 0;
 }
 
@@ -1274,7 +1401,7 @@ constexpr size_t NA_INFO = NA_DEC + 1024;                               // cartr
 constexpr size_t NA_REW = NA_INFO + 256;                                // rewards (internal copy)
 constexpr size_t NA_DONE = NA_REW + 4 * NA_MAX_ENVS;                    // dones (internal copy)
 constexpr size_t NA_CTR = NA_DONE + 256;                                // counters
-constexpr size_t NA_META = NA_CTR + 8 * NA_MAX_ENVS;                    // per frame: records, lines
+constexpr size_t NA_META = NA_CTR + 12 * NA_MAX_ENVS;                   // per frame: records, lines
 constexpr size_t NA_SNAP = NA_META + 16 * NA_MAX_ENVS;                  // per frame: 64-byte snapshot
 constexpr size_t NA_LOG = NA_SNAP + 128 * NA_MAX_ENVS;                  // per frame: TIA-write log
 constexpr size_t NA_BYTES = NA_LOG + (size_t)NA_MAX_ENVS * 2 * NA_LOG_CAP * 4;
@@ -1355,21 +1482,9 @@ extern "C" int atari_step_noalloc(const uint8_t *rom, size_t rom_size, atari_rom
   } else {
     memcpy(img, rom, rom_size);
   }
-  for (int o = 0; o < 256; ++o) {
-    dec[o] = 0;
-    if (!OPMAP[o]) continue;
-    char mn[4] = {OPMAP[o][0], OPMAP[o][1], OPMAP[o][2], 0};
-    uint32_t op = 0, mode = 0;
-    for (uint32_t i = 0; i < sizeof(MNEMONICS) / sizeof(*MNEMONICS); ++i)
-      if (!strcmp(MNEMONICS[i], mn)) op = i;
-    for (uint32_t i = 0; i < sizeof(MODES) / sizeof(*MODES); ++i)
-      if (!strcmp(MODES[i], OPMAP[o] + 4)) mode = i;
-    bool pen;
-    uint32_t cyc = cycles_for(op, mode, pen);
-    dec[o] = op | mode << 8 | cyc << 12 | (pen ? 1u : 0u) << 15;
-  }
+  fill_decode_table(dec);
   memset(info, 0, sizeof info);
-  info[0] = (uint32_t)sc | (uint32_t)(meta.score_addr & 0x7F) << 8 | (uint32_t)(meta.gameover_addr & 0x7F) << 16;
+  info[0] = rom_info_word(rom_size, meta);
   CUDA_TRY(cudaMemcpyAsync(scr + NA_ROM, img, sizeof img, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(scr + NA_DEC, dec, sizeof dec, cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaMemcpyAsync(scr + NA_INFO, info, sizeof info, cudaMemcpyHostToDevice, s));

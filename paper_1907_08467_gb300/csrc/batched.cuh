@@ -126,8 +126,9 @@ __device__ __forceinline__ void fast_step_env(FastConsoleT<SPLIT> &m, uint8_t *s
   if (a.rew_out) a.rew_out[o] = reward;
   if (a.done_out) a.done_out[o] = (uint8_t)done;
   if (a.counters) {
-    a.counters[2 * i] = m.instret;
-    if constexpr (!SPLIT) a.counters[2 * i + 1] = log_total;
+    a.counters[3 * i] = m.instret;
+    a.counters[3 * i + 2] = m.rounds;
+    if constexpr (!SPLIT) a.counters[3 * i + 1] = log_total;
   }
   uint32_t *ewo = reinterpret_cast<uint32_t *>(st + S::EPISODE);
   ewo[1] = step_no + 1;
@@ -187,7 +188,7 @@ __device__ void tia_worker(IoCtx c, const uint32_t *q, int i, const BatchArgs &a
         __threadfence_block();
         vw[IO_ACK] = ++ack;
       } else {
-        if (a.counters) a.counters[2 * i + 1] = log_total;
+        if (a.counters) a.counters[3 * i + 1] = log_total;
         __threadfence_block();
         vw[IO_ACK] = ++ack;
         break;
@@ -309,6 +310,62 @@ __global__ void __launch_bounds__(256, 1) k_interp_split(BatchArgs a) {
       if (cpu) fast_step_env<true>(m, st, i, o, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
       else tia_worker(io, q, i, a);
     }
+  }
+}
+
+// Bank-aware grouping: within each cartridge's run [seg[r], seg[r+1]) of the
+// env list, envs are ordered by the bank their canonical state holds at the
+// start of the step (byte 5, reduced to the cartridge's bank bits), stable in
+// env order, so the lanes of a warp start the step in one bank.  A counting
+// sort with four keys; one block of 256 threads per cartridge.  Cartridges
+// with one bank keep the list as it is.
+__global__ void __launch_bounds__(256) k_group_by_bank(const uint8_t *state, const int32_t *perm_in,
+                                                        const int32_t *seg, const uint32_t *info, int32_t *perm_out) {
+  const int r = blockIdx.x;
+  const int a = seg[r], b = seg[r + 1];
+  const uint32_t banks = info[r] >> 24;
+  if (banks <= 1) {
+    for (int p = a + (int)threadIdx.x; p < b; p += blockDim.x) perm_out[p] = perm_in[p];
+    return;
+  }
+  const uint32_t mask = banks - 1;  // 1 for F8, 3 for F6
+  __shared__ int cnt[4], base[4], wcnt[8][4];
+  if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  for (int p = a + (int)threadIdx.x; p < b; p += blockDim.x)
+    atomicAdd(&cnt[state[(size_t)perm_in[p] * 256 + 5] & mask], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = a;
+    for (int v = 0; v < 4; ++v) { base[v] = s; s += cnt[v]; }
+  }
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int p0 = a; p0 < b; p0 += blockDim.x) {
+    const int p = p0 + (int)threadIdx.x;
+    const bool valid = p < b;
+    const int env = valid ? perm_in[p] : 0;
+    const uint32_t bk = valid ? (state[(size_t)env * 256 + 5] & mask) : 0u;
+    uint32_t rank = 0;
+#pragma unroll
+    for (uint32_t v = 0; v < 4; ++v) {
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, valid && bk == v);
+      if (lane == 0) wcnt[warp][v] = __popc(m);
+      if (valid && bk == v) rank = __popc(m & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    if (valid) {
+      int off = 0;
+      for (uint32_t w2 = 0; w2 < warp; ++w2) off += wcnt[w2][bk];
+      perm_out[base[bk] + off + (int)rank] = env;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+      int t = 0;
+      for (int w2 = 0; w2 < 8; ++w2) t += wcnt[w2][threadIdx.x];
+      base[threadIdx.x] += t;
+    }
+    __syncthreads();
   }
 }
 

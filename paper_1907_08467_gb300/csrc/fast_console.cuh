@@ -443,6 +443,7 @@ struct FastConsoleT {
   uint32_t pend;           // I/O flags of the current instruction
   uint32_t vs_kf;          // cycle of a VSYNC rise in this frame, ~0 if none
   uint32_t status, instret, frame_no;
+  uint32_t rounds;         // lockstep issue rounds of this env's warp in the step (the same on every lane)
   uint32_t wmask;          // lanes of this warp running envs (lockstep issue)
   // split form: this env's TIA event queue and the CPU side's copies
   uint32_t *q;
@@ -495,7 +496,7 @@ struct FastConsoleT {
 #pragma unroll
       for (int b = 0; b < 16; ++b) ram[q * 16 + b] = (ws[b >> 2] >> (8 * (b & 3))) & 0xFF;
     }
-    status = 0; instret = 0; pend = 0; vs_kf = ~0u;
+    status = 0; instret = 0; rounds = 0; pend = 0; vs_kf = ~0u;
     if constexpr (SPLIT) {
       vsync_c = io.T(T_VSYNC);
       vblank_c = io.T(T_VBLANK);
@@ -1105,6 +1106,7 @@ struct FastConsoleT {
       const uint32_t key = active ? (min(kf, 0xFFFEu) << 16 | (PC & 0xFFFFu)) : 0xFFFFFFFFu;
       const uint32_t lead = __reduce_min_sync(wmask, key);
       if (lead == 0xFFFFFFFFu) break;
+      ++rounds;
       if (active && PC == (lead & 0xFFFFu)) {
         if (!exec(w)) fc_exec_general<SPLIT>(this);
         if (jam | (vs_kf != ~0u) | (kf >= 76u * CAP_LINES)) {

@@ -52,8 +52,11 @@ constexpr int POLICY_DEPTH = 9;    // partial-sum stack entries: the tree over 5
 // the same additions of the same operands as the halving tree, hence the same
 // bits.  The block stages chunk c of W, widened to fp32 (exact), in shared
 // memory once for all its envs; every env's 84x84x4 stack is read once.
+// mu_out (may be null) receives the behaviour probability of the sampled
+// action, its weight over the total (fp32 division), for a V-trace buffer.
 __global__ void __launch_bounds__(POLICY_TPB) k_policy(const uint8_t *obs, const uint16_t *W, const uint8_t *state,
-                                                      uint8_t *actions, float *logits_out, int n, uint64_t seed) {
+                                                      uint8_t *actions, float *logits_out, float *mu_out, int n,
+                                                      uint64_t seed) {
   __shared__ float wsm[64 * POLICY_A];
   __shared__ float stk[POLICY_DEPTH * POLICY_A][POLICY_TPB];
   const int t = threadIdx.x;
@@ -122,7 +125,14 @@ __global__ void __launch_bounds__(POLICY_TPB) k_policy(const uint8_t *obs, const
       if (e[j] > 0.0f) last = j;
       if (act < 0 && c > thr) act = j;
     }
-    actions[i] = (uint8_t)(act < 0 ? last : act);
+    const int a = act < 0 ? last : act;
+    actions[i] = (uint8_t)a;
+    if (mu_out) {
+      float ea = e[0];
+#pragma unroll
+      for (int j = 1; j < POLICY_A; ++j) ea = j == a ? e[j] : ea;
+      mu_out[i] = __fdiv_rn(ea, tot);
+    }
     if (logits_out) {
 #pragma unroll
       for (int j = 0; j < POLICY_A; ++j) logits_out[(size_t)i * POLICY_A + j] = l[j];
@@ -130,15 +140,19 @@ __global__ void __launch_bounds__(POLICY_TPB) k_policy(const uint8_t *obs, const
   }
 }
 
-// Append the newest stack plane and the reward of every env to ring slot `slot`.
-__global__ void k_ring_append(const uint8_t *obs, const int32_t *rewards, uint8_t *ring_planes, float *ring_rewards,
-                              int n, int slot) {
+// Append the newest stack plane, the reward and (ring_dones not null) the
+// done flag of every env to ring slot `slot`.
+__global__ void k_ring_append(const uint8_t *obs, const int32_t *rewards, const uint8_t *dones, uint8_t *ring_planes,
+                              float *ring_rewards, uint8_t *ring_dones, int n, int slot) {
   const int i = blockIdx.x;
   if (i >= n) return;
   const uint4 *src = reinterpret_cast<const uint4 *>(obs + (size_t)i * 4 * 7056 + 3 * 7056);
   uint4 *dst = reinterpret_cast<uint4 *>(ring_planes + ((size_t)slot * n + i) * 7056);
   for (int q = threadIdx.x; q < 7056 / 16; q += blockDim.x) dst[q] = src[q];
-  if (threadIdx.x == 0) ring_rewards[(size_t)slot * n + i] = (float)rewards[i];
+  if (threadIdx.x == 0) {
+    ring_rewards[(size_t)slot * n + i] = (float)rewards[i];
+    if (ring_dones) ring_dones[(size_t)slot * n + i] = dones[i];
+  }
 }
 
 }  // namespace atari

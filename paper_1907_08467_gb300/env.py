@@ -28,7 +28,7 @@ class _Config(C.Structure):
                 ("startup_frames", C.c_int), ("max_noops", C.c_int), ("output_mode", C.c_int),
                 ("form", C.c_int), ("log_cap", C.c_int), ("envs_per_block", C.c_int),
                 ("envs_per_warp", C.c_int), ("raster_warps_per_frame", C.c_int), ("seed", C.c_uint64),
-                ("tia_warps", C.c_int)]
+                ("tia_warps", C.c_int), ("grouping", C.c_int)]
 
 
 class _Meta(C.Structure):
@@ -40,11 +40,12 @@ EXPORTS = ["atari_default_config", "atari_env_create", "atari_env_reset", "atari
            "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
            "atari_env_footprint", "atari_env_destroy", "atari_last_error", "atari_env_profile",
            "atari_env_profile_read", "atari_env_launch_shape", "atari_step_noalloc", "atari_env_policy",
-           "atari_env_rollout", "atari_server_default_config", "atari_server_footprint", "atari_server_create",
+           "atari_env_rollout", "atari_env_rollout_ex", "atari_nstep_returns", "atari_vtrace",
+           "atari_server_default_config", "atari_server_footprint", "atari_server_create",
            "atari_server_open", "atari_server_step", "atari_server_close", "atari_server_get_stats",
            "atari_server_destroy", "atari_server_loadgen"]
 PROF_SLOTS = 8
-PROF_NAMES = ["interpreter", "rasteriser", "preprocess", "fused_raster_preprocess", "copy", "policy", "s6", "s7"]
+PROF_NAMES = ["interpreter", "rasteriser", "preprocess", "fused_raster_preprocess", "copy", "policy", "regroup", "s7"]
 
 
 def load_library(path: str | None = None):
@@ -66,7 +67,7 @@ def load_library(path: str | None = None):
         L.atari_env_set_state.argtypes = [P, P, P]
         L.atari_env_get_frames.argtypes = [P, P, P]
         L.atari_env_get_cache.argtypes = [P, P, P]
-        L.atari_env_counters.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), P]
+        L.atari_env_counters.argtypes = [P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), P]
         L.atari_env_info.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.atari_env_footprint.argtypes = [C.c_int, C.c_int, C.POINTER(_Config)]
         L.atari_env_footprint.restype = C.c_size_t
@@ -75,19 +76,24 @@ def load_library(path: str | None = None):
         L.atari_last_error.restype = C.c_char_p
         L.atari_env_profile.argtypes = [P, C.c_int]
         L.atari_env_profile_read.argtypes = [P, P, P]
-        L.atari_env_launch_shape.argtypes = [P, P, P, P, P, P]
+        L.atari_env_launch_shape.argtypes = [P, P, P, P, P, P, P]
         L.atari_step_noalloc.argtypes = [P, C.c_size_t, _Meta, P, P, C.c_int, P, P, P, P, C.c_int, C.c_int,
                                          C.c_int, C.c_uint64, P]
         L.atari_step_noalloc.restype = C.c_int
         L.atari_env_policy.argtypes = [P, P, P, P, P, P]
         L.atari_env_rollout.argtypes = [P, P, C.c_int, P, P, P, P, P, P, C.c_int, C.c_int, P]
+        L.atari_env_rollout_ex.argtypes = [P, P, C.c_int, P, P, P, P, P, P, P, P, C.c_int, C.c_int, P]
+        L.atari_nstep_returns.argtypes = [P, P, C.c_int, C.c_int, P, C.c_int, C.c_int, C.c_float, P, P]
+        L.atari_vtrace.argtypes = [P, P, P, C.c_int, C.c_int, P, P, C.c_int, C.c_int, C.c_float, C.c_float,
+                                   C.c_float, P, P, P]
         from . import server as _srv
         _srv.declare(L)
         for name in ("atari_env_create", "atari_env_reset", "atari_env_step", "atari_env_step_host",
                      "atari_env_status", "atari_env_get_state", "atari_env_set_state",
                      "atari_env_get_frames", "atari_env_get_cache", "atari_env_counters", "atari_env_info",
                      "atari_env_profile", "atari_env_profile_read", "atari_env_launch_shape",
-                     "atari_env_policy", "atari_env_rollout"):
+                     "atari_env_policy", "atari_env_rollout", "atari_env_rollout_ex", "atari_nstep_returns",
+                     "atari_vtrace"):
             getattr(L, name).restype = C.c_int
         if path is None:
             _lib = L
@@ -105,9 +111,9 @@ def _check(rc: int):
 
 def make_config(frameskip=4, sticky=False, n_cache=30, startup_frames=64, max_noops=30,
                 output_mode=OUT_STACK, form=FORM_PLAIN, log_cap=4096, envs_per_block=0, envs_per_warp=0,
-                raster_warps_per_frame=0, seed=1, tia_warps=0) -> _Config:
+                raster_warps_per_frame=0, seed=1, tia_warps=0, grouping=0) -> _Config:
     return _Config(frameskip, int(sticky), n_cache, startup_frames, max_noops, output_mode, form,
-                   log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed, tia_warps)
+                   log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed, tia_warps, grouping)
 
 
 def footprint(n_envs: int, n_roms: int, **cfg) -> int:
@@ -246,9 +252,11 @@ class AtariEnv:
         return out
 
     def counters(self, stream=None):
-        a, b = C.c_uint64(), C.c_uint64()
-        _check(self.lib.atari_env_counters(self.h, C.byref(a), C.byref(b), _stream(stream)))
-        return a.value, b.value
+        """(6502 instructions retired, TIA writes logged, lockstep issue rounds
+        summed over envs) of the last step."""
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(self.lib.atari_env_counters(self.h, C.byref(a), C.byref(b), C.byref(c), _stream(stream)))
+        return a.value, b.value, c.value
 
     def profile(self, enable: bool = True):
         """Record CUDA events around every kernel launch of step()."""
@@ -277,10 +285,19 @@ class AtariEnv:
                                           _ptr(dones), _ptr(ring_planes), _ptr(ring_rewards),
                                           ring_planes.shape[0], ring_start, _stream(stream)))
 
+    def rollout_ex(self, weights, n_steps, obs, actions, rewards, dones, ring_planes, ring_rewards, ring_dones=None,
+                   ring_mu=None, ring_start=0, stream=None):
+        """As rollout(), also keeping each step's dones and the behaviour
+        probability of each sampled action in the ring."""
+        _check(self.lib.atari_env_rollout_ex(self.h, _ptr(weights), n_steps, _ptr(obs), _ptr(actions),
+                                             _ptr(rewards), _ptr(dones), _ptr(ring_planes), _ptr(ring_rewards),
+                                             _ptr(ring_dones), _ptr(ring_mu), ring_planes.shape[0], ring_start,
+                                             _stream(stream)))
+
     def launch_shape(self):
         """(envs per warp, envs per block, warps per frame, interpreter grid,
-        tia_warps: 2 with paired TIA warps, else 1)."""
-        v = [C.c_int() for _ in range(5)]
+        tia_warps: 2 with paired TIA warps, else 1, grouping: 1 env order, 2 bank-aware)."""
+        v = [C.c_int() for _ in range(6)]
         _check(self.lib.atari_env_launch_shape(self.h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)
 
@@ -288,3 +305,28 @@ class AtariEnv:
         n, b = C.c_int(), C.c_size_t()
         _check(self.lib.atari_env_info(self.h, C.byref(n), C.byref(b)))
         return n.value, b.value
+
+
+def nstep_returns(rewards, dones, values, T, gamma, ring_start=0, out=None, stream=None):
+    """Bootstrapped N-step returns [T][n] over a device ring (atari_nstep_returns).
+    rewards, dones: [ring_depth][n]; values: [T + 1][n]."""
+    import torch
+    n = rewards.shape[1]
+    if out is None:
+        out = torch.empty((T, n), dtype=torch.float32, device=rewards.device)
+    _check(load_library().atari_nstep_returns(_ptr(rewards), _ptr(dones), rewards.shape[0], ring_start,
+                                              _ptr(values), T, n, C.c_float(gamma), _ptr(out), _stream(stream)))
+    return out
+
+
+def vtrace(rewards, dones, mu, values, pi, T, gamma, rho_bar=1.0, c_bar=1.0, ring_start=0, stream=None):
+    """V-trace targets and advantages [T][n] over a device ring (atari_vtrace).
+    rewards, dones, mu: [ring_depth][n]; values: [T + 1][n]; pi: [T][n]."""
+    import torch
+    n = rewards.shape[1]
+    vs = torch.empty((T, n), dtype=torch.float32, device=rewards.device)
+    adv = torch.empty((T, n), dtype=torch.float32, device=rewards.device)
+    _check(load_library().atari_vtrace(_ptr(rewards), _ptr(dones), _ptr(mu), rewards.shape[0], ring_start,
+                                       _ptr(values), _ptr(pi), T, n, C.c_float(gamma), C.c_float(rho_bar),
+                                       C.c_float(c_bar), _ptr(vs), _ptr(adv), _stream(stream)))
+    return vs, adv

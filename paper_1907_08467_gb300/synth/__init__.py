@@ -6,3 +6,4 @@ from .roms import (Rom, Workload, workload, actions, luma_table, rom_playfield, 
                    rom_sprite, rom_banked)
 from .fuzz import fuzz_rom  # noqa: F401,E402
 from .policy import policy_weights  # noqa: F401,E402
+from .shared_start import shared_start_states  # noqa: F401,E402

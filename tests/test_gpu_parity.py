@@ -71,6 +71,11 @@ FORMS = {
                             tia_warps=2),
     "split-8x16-w2": dict(form=FORM_BATCHED, envs_per_warp=8, envs_per_block=16, raster_warps_per_frame=2,
                           tia_warps=2),
+    # bank-aware grouping: the env list re-sorted by bank at every step
+    "split-32x128-w4-bank": dict(form=FORM_BATCHED, envs_per_warp=32, envs_per_block=128, raster_warps_per_frame=4,
+                                 tia_warps=2, grouping=2),
+    "batched-8x16-w1-bank": dict(form=FORM_BATCHED, envs_per_warp=8, envs_per_block=16, raster_warps_per_frame=1,
+                                 grouping=2),
 }
 
 
@@ -124,12 +129,15 @@ def test_sprite_family_stack_output(form):
     run_parity(g, o, acts, check_frames=True, check_state_every=1)
 
 
-@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-8x16-w1", "split-8x16-w2"])
+@pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-8x16-w1", "split-8x16-w2", "split-32x128-w4-bank",
+                                  "batched-8x16-w1-bank"])
 def test_banked_sticky_family(form):
     """32 cartridges mixing 4 KB, F8 and F6 with code in every bank, RIOT-timer
     frame timing and sticky actions drawn from the per-env Philox stream."""
     w = synth.workload(3, n_envs=64)
     g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, sticky=True, seed=w.seed, **FORMS[form])
+    if form.endswith("bank"):
+        assert g.launch_shape()[5] == 2      # the env list is regrouped by bank every step
     acts = synth.actions(13, 80, 64)
     run_parity(g, o, acts, check_frames=True)
 
@@ -144,30 +152,6 @@ def test_fuzz_programs(seed0, form):
     g, o = pair(roms, env_rom, output_mode=OUT_STACK, seed=5, **FORMS[form])
     acts = synth.actions(14 + seed0, 60, 64)
     run_parity(g, o, acts, check_frames=True)
-
-
-@pytest.mark.parametrize("form", ["plain", "batched-auto"])
-def test_full_size_sprite_config_sampled(form):
-    """The 4096-env, 8-ROM configuration in the launch configuration the
-    benchmark times: 25 steps, all envs free of faults, and 40 sampled envs
-    (their own env keys) equal to the oracle run on just those envs."""
-    w = synth.workload(2)
-    n = w.n_envs
-    luma = synth.luma_table()
-    g = AtariEnv.from_workload(w, **FORMS[form])
-    rng = np.random.default_rng(3)
-    idx = np.sort(rng.choice(n, 40, replace=False))
-    o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
-                   [w.env_rom[i] for i in idx], luma=luma, env_key=idx, seed=w.seed)
-    acts = synth.actions(15, 25, n)
-    for s in range(25):
-        obs, rew, done = g.step(torch.from_numpy(acts[s]).cuda())
-        oo, orw, od = o.step(acts[s][idx], n_threads=8)
-        assert_same(f"step {s} rewards", rew.cpu().numpy()[idx], orw)
-        assert_same(f"step {s} dones", done.cpu().numpy()[idx], od)
-        assert_same(f"step {s} obs", obs.cpu().numpy()[idx], oo)
-    assert_same("state", g.state().cpu().numpy()[idx], o.state())
-    assert int(g.status().abs().sum().item()) == 0
 
 
 @pytest.mark.parametrize("n,form", [(1, "plain"), (37, "plain"), (1, "batched-auto"), (37, "batched-32x128-w4"),
@@ -261,7 +245,7 @@ def test_batched_equals_plain_at_full_size():
     assert torch.equal(a.state(), b.state())
 
 
-@pytest.mark.parametrize("form", ["plain", "batched-auto"])
+@pytest.mark.parametrize("form", ["plain", "batched-auto", "split-32x128-w4-bank"])
 def test_state_with_extra_bank_bits_matches_oracle(form):
     """States whose bank byte has bits the cartridge does not latch (4 KB, F8
     and F6 envs) load as the cartridge's bits on both sides and step alike."""
@@ -283,30 +267,6 @@ def test_state_with_extra_bank_bits_matches_oracle(form):
     assert_same("dones", done.cpu().numpy(), od)
     assert_same("obs", obs.cpu().numpy(), oo)
     run_parity(g, o, acts[2:])
-
-
-def test_full_size_banked_config_sampled():
-    """The 32768-env, 32-cartridge banked configuration with sticky actions
-    in the benchmark's launch configuration (autotuned batched form): 10
-    steps, no env faults, and 48 sampled envs (3 of every other cartridge,
-    own env keys) equal to the oracle run on just those envs."""
-    w = synth.workload(3)
-    n = w.n_envs
-    g = AtariEnv.from_workload(w, form=FORM_BATCHED)
-    rng = np.random.default_rng(31)
-    idx = np.sort(np.concatenate([rng.choice(np.flatnonzero(np.asarray(w.env_rom) == r), 3, replace=False)
-                                  for r in range(0, 32, 2)]))
-    o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
-                   [w.env_rom[i] for i in idx], luma=synth.luma_table(), env_key=idx, sticky=True, seed=w.seed)
-    acts = synth.actions(33, 10, n)
-    for s in range(10):
-        obs, rew, done = g.step(torch.from_numpy(acts[s]).cuda())
-        oo, orw, od = o.step(acts[s][idx], n_threads=8)
-        assert_same(f"step {s} rewards", rew.cpu().numpy()[idx], orw)
-        assert_same(f"step {s} dones", done.cpu().numpy()[idx], od)
-        assert_same(f"step {s} obs", obs.cpu().numpy()[idx], oo)
-    assert_same("state", g.state().cpu().numpy()[idx], o.state())
-    assert int(g.status().abs().sum().item()) == 0
 
 
 def test_split_form_bounded_waits_report_stall():

@@ -70,38 +70,3 @@ def test_rollout_ring_matches_oracle_loop():
     assert np.array_equal(ring.cpu().numpy(), ring_h)
     assert np.array_equal(ring_r.cpu().numpy(), ring_rh)
     assert np.array_equal(g.state().cpu().numpy(), o.state())
-
-
-def test_full_size_inference_loop_sampled():
-    """The 16384-env inference loop as the benchmark runs it (one rollout
-    iteration per step: policy, step, ring append) for 4 steps; 24 sampled
-    envs equal the oracle loop run on just those envs: actions, stacks,
-    rewards, dones, ring planes and rewards, final state."""
-    w = synth.workload(5)
-    n, T, R = w.n_envs, 4, 5
-    g = AtariEnv.from_workload(w, form=FORM_BATCHED)
-    rng = np.random.default_rng(55)
-    idx = np.sort(rng.choice(n, 24, replace=False))
-    o = OracleEnvs([r.data for r in w.roms], [r.score_addr for r in w.roms], [r.gameover_addr for r in w.roms],
-                   [w.env_rom[i] for i in idx], luma=synth.luma_table(), env_key=idx, seed=w.seed)
-    W = synth.policy_weights(w.seed)
-    Wd = torch.from_numpy(W.view(np.int16)).cuda()
-    obs = torch.zeros((n, 4, 84, 84), dtype=torch.uint8, device="cuda")
-    act = torch.empty(n, dtype=torch.uint8, device="cuda")
-    rew = torch.empty(n, dtype=torch.int32, device="cuda")
-    done = torch.empty(n, dtype=torch.uint8, device="cuda")
-    ring = torch.zeros((R, n, 84 * 84), dtype=torch.uint8, device="cuda")
-    ring_r = torch.zeros((R, n), dtype=torch.float32, device="cuda")
-    obs_h = np.zeros((len(idx), 4, 84, 84), np.uint8)
-    for t in range(T):
-        g.rollout(Wd, 1, obs, act, rew, done, ring, ring_r, ring_start=t)
-        a, _ = o.policy(obs_h, W, n_threads=8)
-        obs_h, r, d = o.step(a, n_threads=8)
-        torch.cuda.synchronize()
-        assert np.array_equal(act.cpu().numpy()[idx], a), t
-        assert np.array_equal(obs.cpu().numpy()[idx], obs_h), t
-        assert np.array_equal(rew.cpu().numpy()[idx], r), t
-        assert np.array_equal(done.cpu().numpy()[idx], d), t
-        assert np.array_equal(ring[t % R].cpu().numpy()[idx], obs_h[:, 3].reshape(len(idx), -1)), t
-        assert np.array_equal(ring_r[t % R].cpu().numpy()[idx], r.astype(np.float32)), t
-    assert np.array_equal(g.state().cpu().numpy()[idx], o.state())

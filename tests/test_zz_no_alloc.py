@@ -6,7 +6,8 @@ cannot create an env.  atari_step_noalloc takes their own state, start-state,
 action and output buffers and keeps its scratch in a fixed array inside the
 library.  This test checks it against the regular entry point (a plain-form
 env with palette output) on the same states and actions, two calls in a row,
-and that those calls take no device memory.  It sits in a file pytest
+and that those calls take no device memory, for every cartridge size it
+accepts (2 KB, 4 KB, F8, F6) with and without sticky actions.  It sits in a file pytest
 collects last.
 """
 import ctypes as C
@@ -25,29 +26,78 @@ def _p(t):
     return C.c_void_p(t.data_ptr())
 
 
-@pytest.mark.parametrize("config,n", [(1, 16), (2, 37)])
-def test_noalloc_step_matches_env_step(config, n):
+ROM_2K = """
+        .org $F800
+Start:  LDX #$FF
+        TXS
+        LDA #0
+        STA $80
+        STA $81
+Frame:  LDA #2
+        STA WSYNC
+        STA VSYNC
+        STA WSYNC
+        STA WSYNC
+        STA WSYNC
+        LDA #0
+        STA VSYNC
+        STA VBLANK
+        LDA SWCHA
+        AND #$80
+        BNE NoR
+        INC $80
+NoR:    INC $82
+        LDX #250
+Lines:  STA WSYNC
+        STX COLUBK
+        TXA
+        ADC $82
+        STA PF1
+        DEX
+        BNE Lines
+        JMP Frame
+        .org $FFFA
+        .word Start, Start, Start
+"""
+
+
+def _cartridge(config, which):
+    """(image, score address, game-over address, seed): a workload's cartridge,
+    or a 2 KB image (mirrored into both halves of the 4 KB window)."""
+    if config == 0:
+        return synth.Assembler().assemble(ROM_2K, org=0xF800, size=2048), 0x80, 0x81, 7
+    w = synth.workload(config, n_envs=32)
+    r = w.roms[which]
+    return r.data, r.score_addr, r.gameover_addr, w.seed
+
+
+# (workload config, cartridge, envs, sticky): 4 KB playfield and sprite
+# cartridges, an 8 KB F8 and a 16 KB F6 banked cartridge with sticky actions,
+# and a 2 KB image
+@pytest.mark.parametrize("config,which,n,sticky", [(1, 0, 16, 0), (2, 0, 37, 0), (3, 12, 24, 1), (3, 22, 24, 1),
+                                                   (0, 0, 8, 1)])
+def test_noalloc_step_matches_env_step(config, which, n, sticky):
     lib = load_library()
-    w = synth.workload(config, n_envs=n)
-    rom = w.roms[0]
-    env = AtariEnv([rom.data], [(rom.score_addr, rom.gameover_addr)], [0] * n, luma=synth.luma_table(),
-                   form=FORM_PLAIN, output_mode=OUT_PALETTE, seed=w.seed)
+    data, score_addr, gameover_addr, seed = _cartridge(config, which)
+    assert len(data) == {0: 2048, 1: 4096, 2: 4096, 3: 8192 if which < 22 else 16384}[config]
+    env = AtariEnv([data], [(score_addr, gameover_addr)], [0] * n, luma=synth.luma_table(),
+                   form=FORM_PLAIN, output_mode=OUT_PALETTE, seed=seed, sticky=bool(sticky))
     states = env.state().clone()
     cache = env.cache()[0].contiguous()
     frame = torch.empty((n, 210, 160), dtype=torch.uint8, device="cuda")
     rew = torch.empty(n, dtype=torch.int32, device="cuda")
     done = torch.empty(n, dtype=torch.uint8, device="cuda")
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rom_buf = C.create_string_buffer(rom.data, len(rom.data))
-    meta = _Meta(rom.score_addr, rom.gameover_addr)
-    acts = synth.actions(40 + config, 2, n)
+    rom_buf = C.create_string_buffer(data, len(data))
+    meta = _Meta(score_addr, gameover_addr)
+    acts = synth.actions(40 + config + which, 2, n)
     for call in range(2):
         a = torch.from_numpy(acts[call]).cuda()
         obs_ref, rew_ref, done_ref = env.step(a)
         torch.cuda.synchronize()
         free_before = torch.cuda.mem_get_info()[0]
-        rc = lib.atari_step_noalloc(rom_buf, len(rom.data), meta, _p(states), _p(cache), cache.shape[0], _p(a),
-                                    _p(frame), _p(rew), _p(done), n, 4, 0, w.seed, stream)
+        rc = lib.atari_step_noalloc(rom_buf, len(data), meta, _p(states), _p(cache), cache.shape[0], _p(a),
+                                    _p(frame), _p(rew), _p(done), n, 4, sticky, seed, stream)
         assert rc == 0, lib.atari_last_error()
         torch.cuda.synchronize()
         if call == 1:   # the first call may load the library's device module, which holds the array
