@@ -39,8 +39,10 @@
  *       (0xFF - (n - (v+1) I)) & 0xFF with the TIMINT flag (bit 7) set.
  *   R11 power-on: registers and RAM 0, SP = 0xFD, P = 0x24, bank 0, PC from
  *       the reset vector, timer 0 with interval 1024 written at cycle 0.
- *   R12 undocumented opcodes halt the CPU (JAM, status ILLEGAL); the env is
- *       done at the end of every step it ends halted, which also sets ILLEGAL.
+ *   R12 the stable undocumented opcodes of the NMOS part execute per their
+ *       published descriptions (see UNDOC below); the other 21 opcodes halt
+ *       the CPU (JAM, status ILLEGAL); the env is done at the end of every
+ *       step it ends halted, which also sets ILLEGAL.
  *   R13 decimal mode follows the NMOS behaviour described by B. Clark
  *       ("Decimal Mode", 6502.org): A and C by nibble adjustment, N and V
  *       from the intermediate result of ADC, Z (and all SBC flags) binary.
@@ -124,7 +126,7 @@ struct orc_machine {
     uint32_t status;
 };
 
-/* ---- opcode table: documented NMOS 6502 ---- */
+/* ---- opcode table: documented NMOS 6502, plus the stable undocumented opcodes ---- */
 enum {
     M_IMP, M_ACC, M_IMM, M_ZP, M_ZPX, M_ZPY, M_ABS, M_ABX, M_ABY, M_IND, M_IZX, M_IZY, M_REL
 };
@@ -133,7 +135,9 @@ enum {
     O_CLC, O_CLD, O_CLI, O_CLV, O_CMP, O_CPX, O_CPY, O_DEC, O_DEX, O_DEY, O_EOR, O_INC, O_INX,
     O_INY, O_JMP, O_JSR, O_LDA, O_LDX, O_LDY, O_LSR, O_NOP, O_ORA, O_PHA, O_PHP, O_PLA, O_PLP,
     O_ROL, O_ROR, O_RTI, O_RTS, O_SBC, O_SEC, O_SED, O_SEI, O_STA, O_STX, O_STY, O_TAX, O_TAY,
-    O_TSX, O_TXA, O_TXS, O_TYA
+    O_TSX, O_TXA, O_TXS, O_TYA,
+    /* undocumented NMOS operations with a stable, published behaviour */
+    O_SLO, O_RLA, O_SRE, O_RRA, O_SAX, O_LAX, O_DCP, O_ISC, O_ANC, O_ALR, O_SBX
 };
 typedef struct { uint8_t op, mode, cycles; } opinfo;
 static const uint8_t MODE_LEN[13] = {1, 1, 2, 2, 2, 2, 3, 3, 3, 3, 2, 2, 2};
@@ -190,6 +194,46 @@ static const uint8_t DOC[151][4] = {
     {0xAA,O_TAX,M_IMP,2},{0xA8,O_TAY,M_IMP,2},{0xBA,O_TSX,M_IMP,2},{0x8A,O_TXA,M_IMP,2},
     {0x9A,O_TXS,M_IMP,2},{0x98,O_TYA,M_IMP,2},
 };
+/* The stable undocumented opcodes of the NMOS part (opcode, operation, mode,
+ * base cycles), per the published descriptions of its undocumented
+ * instructions: a read-modify-write of memory followed by an accumulator
+ * operation (SLO = ASL + ORA, RLA = ROL + AND, SRE = LSR + EOR, RRA = ROR +
+ * ADC, DCP = DEC + CMP, ISC = INC + SBC; always the long cycle count), SAX
+ * (store A AND X), LAX (load A and X), ANC (AND, carry = bit 7), ALR (AND
+ * then LSR), SBX (X = (A AND X) - operand, flags as CMP), SBC $EB, and the
+ * NOPs of one to three bytes (those with a memory operand read it).  The
+ * remaining 21 opcodes (12 that halt the part, and ANE, LXA, SHA, SHX, SHY,
+ * TAS, LAS, ARR, whose results depend on the chip or, for ARR, on a decimal
+ * mode that is not described consistently) stay unmodelled: they halt. */
+static const uint8_t UNDOC[84][4] = {
+    {0x07,O_SLO,M_ZP,5},{0x17,O_SLO,M_ZPX,6},{0x0F,O_SLO,M_ABS,6},{0x1F,O_SLO,M_ABX,7},
+    {0x1B,O_SLO,M_ABY,7},{0x03,O_SLO,M_IZX,8},{0x13,O_SLO,M_IZY,8},
+    {0x27,O_RLA,M_ZP,5},{0x37,O_RLA,M_ZPX,6},{0x2F,O_RLA,M_ABS,6},{0x3F,O_RLA,M_ABX,7},
+    {0x3B,O_RLA,M_ABY,7},{0x23,O_RLA,M_IZX,8},{0x33,O_RLA,M_IZY,8},
+    {0x47,O_SRE,M_ZP,5},{0x57,O_SRE,M_ZPX,6},{0x4F,O_SRE,M_ABS,6},{0x5F,O_SRE,M_ABX,7},
+    {0x5B,O_SRE,M_ABY,7},{0x43,O_SRE,M_IZX,8},{0x53,O_SRE,M_IZY,8},
+    {0x67,O_RRA,M_ZP,5},{0x77,O_RRA,M_ZPX,6},{0x6F,O_RRA,M_ABS,6},{0x7F,O_RRA,M_ABX,7},
+    {0x7B,O_RRA,M_ABY,7},{0x63,O_RRA,M_IZX,8},{0x73,O_RRA,M_IZY,8},
+    {0xC7,O_DCP,M_ZP,5},{0xD7,O_DCP,M_ZPX,6},{0xCF,O_DCP,M_ABS,6},{0xDF,O_DCP,M_ABX,7},
+    {0xDB,O_DCP,M_ABY,7},{0xC3,O_DCP,M_IZX,8},{0xD3,O_DCP,M_IZY,8},
+    {0xE7,O_ISC,M_ZP,5},{0xF7,O_ISC,M_ZPX,6},{0xEF,O_ISC,M_ABS,6},{0xFF,O_ISC,M_ABX,7},
+    {0xFB,O_ISC,M_ABY,7},{0xE3,O_ISC,M_IZX,8},{0xF3,O_ISC,M_IZY,8},
+    {0x87,O_SAX,M_ZP,3},{0x97,O_SAX,M_ZPY,4},{0x8F,O_SAX,M_ABS,4},{0x83,O_SAX,M_IZX,6},
+    {0xA7,O_LAX,M_ZP,3},{0xB7,O_LAX,M_ZPY,4},{0xAF,O_LAX,M_ABS,4},{0xBF,O_LAX,M_ABY,4},
+    {0xA3,O_LAX,M_IZX,6},{0xB3,O_LAX,M_IZY,5},
+    {0x0B,O_ANC,M_IMM,2},{0x2B,O_ANC,M_IMM,2},{0x4B,O_ALR,M_IMM,2},{0xCB,O_SBX,M_IMM,2},
+    {0xEB,O_SBC,M_IMM,2},
+    {0x1A,O_NOP,M_IMP,2},{0x3A,O_NOP,M_IMP,2},{0x5A,O_NOP,M_IMP,2},{0x7A,O_NOP,M_IMP,2},
+    {0xDA,O_NOP,M_IMP,2},{0xFA,O_NOP,M_IMP,2},
+    {0x80,O_NOP,M_IMM,2},{0x82,O_NOP,M_IMM,2},{0x89,O_NOP,M_IMM,2},{0xC2,O_NOP,M_IMM,2},
+    {0xE2,O_NOP,M_IMM,2},
+    {0x04,O_NOP,M_ZP,3},{0x44,O_NOP,M_ZP,3},{0x64,O_NOP,M_ZP,3},
+    {0x14,O_NOP,M_ZPX,4},{0x34,O_NOP,M_ZPX,4},{0x54,O_NOP,M_ZPX,4},{0x74,O_NOP,M_ZPX,4},
+    {0xD4,O_NOP,M_ZPX,4},{0xF4,O_NOP,M_ZPX,4},
+    {0x0C,O_NOP,M_ABS,4},
+    {0x1C,O_NOP,M_ABX,4},{0x3C,O_NOP,M_ABX,4},{0x5C,O_NOP,M_ABX,4},{0x7C,O_NOP,M_ABX,4},
+    {0xDC,O_NOP,M_ABX,4},{0xFC,O_NOP,M_ABX,4},
+};
 static opinfo OPS[256];
 static pthread_once_t ops_once = PTHREAD_ONCE_INIT;
 static void build_ops(void) {
@@ -198,6 +242,11 @@ static void build_ops(void) {
         OPS[DOC[i][0]].op = DOC[i][1];
         OPS[DOC[i][0]].mode = DOC[i][2];
         OPS[DOC[i][0]].cycles = DOC[i][3];
+    }
+    for (int i = 0; i < 84; i++) {
+        OPS[UNDOC[i][0]].op = UNDOC[i][1];
+        OPS[UNDOC[i][0]].mode = UNDOC[i][2];
+        OPS[UNDOC[i][0]].cycles = UNDOC[i][3];
     }
 }
 int orc_base_cycles(uint8_t opcode) {
@@ -541,7 +590,7 @@ static uint8_t compare(uint8_t p, uint8_t r, uint8_t v) {
 static int is_read_op(int op) {
     switch (op) {
     case O_LDA: case O_LDX: case O_LDY: case O_ADC: case O_SBC: case O_AND: case O_ORA:
-    case O_EOR: case O_CMP: case O_CPX: case O_CPY: case O_BIT: return 1;
+    case O_EOR: case O_CMP: case O_CPX: case O_CPY: case O_BIT: case O_LAX: case O_NOP: return 1;
     default: return 0;
     }
 }
@@ -663,6 +712,60 @@ static int cpu_exec(orc_machine *m) {
         else { bus_write(m, ea, old, kA - 1); bus_write(m, ea, r, kA); }
         break;
     }
+    case O_SLO: case O_RLA: case O_SRE: case O_RRA: case O_DCP: case O_ISC: {
+        /* read-modify-write of memory (old value written back first, as the
+         * documented RMW instructions do), then the accumulator operation */
+        uint8_t old = bus_read(m, ea, kA - 2), r;
+        uint8_t c = m->p & F_C;
+        switch (oi.op) {
+        case O_SLO: r = (uint8_t)(old << 1); c = old >> 7; break;
+        case O_RLA: r = (uint8_t)(old << 1 | (m->p & F_C)); c = old >> 7; break;
+        case O_SRE: r = old >> 1; c = old & 1; break;
+        case O_RRA: r = (uint8_t)(old >> 1 | (m->p & F_C) << 7); c = old & 1; break;
+        case O_DCP: r = (uint8_t)(old - 1); break;
+        default: r = (uint8_t)(old + 1); break;
+        }
+        bus_write(m, ea, old, kA - 1);
+        bus_write(m, ea, r, kA);
+        switch (oi.op) {
+        case O_SLO: m->a |= r; m->p = set_nz((uint8_t)((m->p & ~F_C) | c), m->a); break;
+        case O_RLA: m->a &= r; m->p = set_nz((uint8_t)((m->p & ~F_C) | c), m->a); break;
+        case O_SRE: m->a ^= r; m->p = set_nz((uint8_t)((m->p & ~F_C) | c), m->a); break;
+        case O_RRA: {
+            uint32_t s2 = orc_alu_adc(m->a, r, (uint8_t)((m->p & ~F_C) | c));
+            m->a = (uint8_t)s2;
+            m->p = (uint8_t)((s2 >> 8) | F_U);
+            break;
+        }
+        case O_DCP: m->p = compare(m->p, m->a, r); break;
+        default: {
+            uint32_t s2 = orc_alu_sbc(m->a, r, m->p);
+            m->a = (uint8_t)s2;
+            m->p = (uint8_t)((s2 >> 8) | F_U);
+            break;
+        }
+        }
+        break;
+    }
+    case O_SAX: bus_write(m, ea, m->a & m->x, kA); break;
+    case O_LAX: m->a = m->x = bus_read(m, ea, kA); m->p = set_nz(m->p, m->a); break;
+    case O_ANC: m->a &= b1; m->p = set_nz(m->p, m->a); m->p = (uint8_t)((m->p & ~F_C) | (m->a >> 7)); break;
+    case O_ALR:
+        m->a &= b1;
+        m->p = (uint8_t)((m->p & ~F_C) | (m->a & 1));
+        m->a >>= 1;
+        m->p = set_nz(m->p, m->a);
+        break;
+    case O_SBX: {
+        uint8_t ax = m->a & m->x;
+        m->p = (uint8_t)((m->p & ~F_C) | (ax >= b1 ? F_C : 0));
+        m->x = (uint8_t)(ax - b1);
+        m->p = set_nz(m->p, m->x);
+        break;
+    }
+    case O_NOP:
+        if (oi.mode != M_IMP && oi.mode != M_IMM) (void)bus_read(m, ea, kA);  /* the operand read */
+        break;
     case O_INX: m->x++; m->p = set_nz(m->p, m->x); break;
     case O_INY: m->y++; m->p = set_nz(m->p, m->y); break;
     case O_DEX: m->x--; m->p = set_nz(m->p, m->x); break;
@@ -680,7 +783,6 @@ static int cpu_exec(orc_machine *m) {
     case O_CLV: m->p &= (uint8_t)~F_V; break;
     case O_CLD: m->p &= (uint8_t)~F_D; break;
     case O_SED: m->p |= F_D; break;
-    case O_NOP: break;
     case O_PHA: push(m, m->a, kA); break;
     case O_PHP: push(m, m->p | F_B | F_U, kA); break;
     case O_PLA: m->a = pull(m, kA); m->p = set_nz(m->p, m->a); break;

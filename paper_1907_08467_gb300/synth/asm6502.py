@@ -72,6 +72,21 @@ OPCODES = {
     "TXS": {"imp": 0x9A}, "TYA": {"imp": 0x98},
 }
 
+# Stable undocumented NMOS operations (for cartridges and tests that use
+# them); the assembler accepts these mnemonics as well.
+UNDOC_OPCODES = {
+    "SLO": {"zp": 0x07, "zpx": 0x17, "abs": 0x0F, "abx": 0x1F, "aby": 0x1B, "izx": 0x03, "izy": 0x13},
+    "RLA": {"zp": 0x27, "zpx": 0x37, "abs": 0x2F, "abx": 0x3F, "aby": 0x3B, "izx": 0x23, "izy": 0x33},
+    "SRE": {"zp": 0x47, "zpx": 0x57, "abs": 0x4F, "abx": 0x5F, "aby": 0x5B, "izx": 0x43, "izy": 0x53},
+    "RRA": {"zp": 0x67, "zpx": 0x77, "abs": 0x6F, "abx": 0x7F, "aby": 0x7B, "izx": 0x63, "izy": 0x73},
+    "DCP": {"zp": 0xC7, "zpx": 0xD7, "abs": 0xCF, "abx": 0xDF, "aby": 0xDB, "izx": 0xC3, "izy": 0xD3},
+    "ISC": {"zp": 0xE7, "zpx": 0xF7, "abs": 0xEF, "abx": 0xFF, "aby": 0xFB, "izx": 0xE3, "izy": 0xF3},
+    "SAX": {"zp": 0x87, "zpy": 0x97, "abs": 0x8F, "izx": 0x83},
+    "LAX": {"zp": 0xA7, "zpy": 0xB7, "abs": 0xAF, "aby": 0xBF, "izx": 0xA3, "izy": 0xB3},
+    "ANC": {"imm": 0x0B}, "ALR": {"imm": 0x4B}, "SBX": {"imm": 0xCB},
+}
+ALL_OPCODES = {**OPCODES, **UNDOC_OPCODES}
+
 MODE_SIZE = {"imp": 1, "acc": 1, "imm": 2, "zp": 2, "zpx": 2, "zpy": 2, "abs": 3, "abx": 3,
              "aby": 3, "ind": 3, "izx": 2, "izy": 2, "rel": 2}
 
@@ -127,7 +142,7 @@ class Assembler:
             return None
 
     def _parse_operand(self, mne: str, opnd: str, env: dict, strict: bool, force_abs: bool):
-        modes = OPCODES[mne]
+        modes = ALL_OPCODES[mne]
         o = opnd.strip()
         if o == "" or o.upper() == "A":
             if "acc" in modes:
@@ -224,14 +239,14 @@ class Assembler:
                 force_abs = mne.endswith(".W")
                 if force_abs:
                     mne = mne[:-2]
-                if mne not in OPCODES:
+                if mne not in ALL_OPCODES:
                     raise AsmError(f"unknown mnemonic '{mne}' in '{line}'")
                 if pass_no == 2 and modes1.get(li) in ("abs", "abx", "aby"):
                     force_abs = True  # keep the size chosen in pass 1 (forward reference)
                 mode, v = self._parse_operand(mne, parts[1] if len(parts) > 1 else "", env, strict, force_abs)
                 if pass_no == 1:
                     modes1[li] = mode
-                op = OPCODES[mne][mode]
+                op = ALL_OPCODES[mne][mode]
                 n = MODE_SIZE[mode]
                 self._emit(image, org, size, pc, op, strict)
                 if mode == "rel":

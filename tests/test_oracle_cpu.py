@@ -125,11 +125,13 @@ def test_decimal_adc_n_and_v_worked_cases():
 
 
 def test_documented_opcode_set():
-    """Exactly the 151 documented opcodes have a cycle count; the other 105 JAM."""
+    """The 151 documented opcodes all have a cycle count (the stable
+    undocumented ones and the opcodes that halt are pinned in
+    test_oracle_undocumented.py)."""
     doc = {op for modes in OPCODES.values() for op in modes.values()}
     assert len(doc) == 151
-    for op in range(256):
-        assert (base_cycles(op) > 0) == (op in doc), hex(op)
+    for op in doc:
+        assert base_cycles(op) > 0, hex(op)
 
 
 # Documented timing rules per (class, addressing mode).
