@@ -95,7 +95,7 @@ struct orc_machine {
     /* cartridge */
     const uint8_t *rom;
     uint32_t rom_size;
-    int scheme;            /* 0: 2K/4K, 1: F8, 2: F6 */
+    int scheme;            /* 0: 2K/4K, 1: F8, 2: F6, 3: F4 */
     uint8_t bank;
     /* RIOT */
     uint8_t ram[128];
@@ -556,6 +556,7 @@ static void riot_write(orc_machine *m, uint16_t addr, uint8_t v, uint64_t t) {
 static void cart_hotspot(orc_machine *m, uint16_t off) {
     if (m->scheme == 1 && (off == 0xFF8 || off == 0xFF9)) m->bank = (uint8_t)(off - 0xFF8);
     if (m->scheme == 2 && off >= 0xFF6 && off <= 0xFF9) m->bank = (uint8_t)(off - 0xFF6);
+    if (m->scheme == 3 && off >= 0xFF4 && off <= 0xFFB) m->bank = (uint8_t)(off - 0xFF4);
 }
 static uint8_t cart_byte(const orc_machine *m, uint16_t off) {
     if (m->rom_size == 2048) return m->rom[off & 0x7FF];
@@ -843,6 +844,7 @@ static int scheme_of(size_t size) {
     if (size == 2048 || size == 4096) return 0;
     if (size == 8192) return 1;
     if (size == 16384) return 2;
+    if (size == 32768) return 3;
     return -1;
 }
 
@@ -956,8 +958,9 @@ static void pack_machine(const orc_machine *m, uint8_t *o) {
 
 static void unpack_machine(orc_machine *m, const uint8_t *o) {
     m->a = o[0x00]; m->x = o[0x01]; m->y = o[0x02]; m->sp = o[0x03]; m->p = o[0x04];
-    /* the cartridge latches only its own bank bits: one for F8, two for F6 */
-    m->bank = (uint8_t)(o[0x05] & (m->scheme == 2 ? 3u : m->scheme == 1 ? 1u : 0u)); m->pc = get16(o + 0x06);
+    /* the cartridge latches only its own bank bits: one for F8, two for F6, three for F4 */
+    m->bank = (uint8_t)(o[0x05] & (m->scheme == 3 ? 7u : m->scheme == 2 ? 3u : m->scheme == 1 ? 1u : 0u));
+    m->pc = get16(o + 0x06);
     m->k = get64(o + 0x08);
     m->tim_cw = get64(o + 0x10);
     m->tim_v = o[0x18]; m->tim_shift = o[0x19]; m->swcha_out = o[0x1A]; m->swacnt = o[0x1B];

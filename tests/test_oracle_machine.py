@@ -447,6 +447,30 @@ Start:  LDA #{b}
     assert m.ram()[0] == 0 and m.state()[0x05] == 1
 
 
+def test_bank_switch_f4_all_banks():
+    """F4 (32 KB, 8 banks): reading $1FF4 + j selects bank j.  Bank b stores b
+    at $80 + b, then reads the hotspot of bank b + 1; the next instruction
+    ($F007) comes from that bank, which jumps to its own Start.  Bank 7
+    selects bank 0, whose $F007 halts.  Every hotspot is visited once."""
+    banks = []
+    for b in range(8):
+        nxt = (b + 1) % 8
+        tail = "        .byte $02\n" if b == 0 else "        JMP Start\n"
+        banks.append(Assembler().assemble(f"""
+        .org $F000
+Start:  LDA #{b}
+        STA $80+{b}
+        LDA ${0x1FF4 + nxt:04X}
+        .org $F007
+""" + tail + """
+        .org $FFFA
+        .word Start, Start, Start
+""", org=0xF000, size=4096))
+    m = OracleMachine(b"".join(banks))
+    run_to_jam(m)
+    assert list(m.ram()[:8]) == list(range(8)) and m.state()[0x05] == 0
+
+
 ALE = ["NOOP", "FIRE", "UP", "RIGHT", "LEFT", "DOWN", "UPRIGHT", "UPLEFT", "DOWNRIGHT", "DOWNLEFT",
        "UPFIRE", "RIGHTFIRE", "LEFTFIRE", "DOWNFIRE", "UPRIGHTFIRE", "UPLEFTFIRE", "DOWNRIGHTFIRE",
        "DOWNLEFTFIRE"]
@@ -513,9 +537,10 @@ Start:  LDA #$F0
 
 
 def test_state_bank_byte_keeps_only_the_cartridges_bank_bits():
-    """A 2K/4K cartridge has no bank latch, F8 one bank bit and F6 two: a
-    state whose bank byte has more bits set loads as those bits only."""
-    for size, mask in [(2048, 0), (4096, 0), (8192, 1), (16384, 3)]:
+    """A 2K/4K cartridge has no bank latch, F8 one bank bit, F6 two and F4
+    three: a state whose bank byte has more bits set loads as those bits
+    only."""
+    for size, mask in [(2048, 0), (4096, 0), (8192, 1), (16384, 3), (32768, 7)]:
         m = OracleMachine(bytes(size))
         for b in (0xFF, 0xFE, 0x05, 0x02):
             s = m.state()
