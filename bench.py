@@ -49,7 +49,9 @@ SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 # A shape captured on another workload is used with its source named; a shape
 # never captured reports achieved = null.
 INTERP_CAPTURES = {
-    # (kernel, envs per warp, config): (warp-inst per 6502 instruction, DRAM bytes per env-step)
+    # (kernel, envs per warp, opcode dispatch, config): (warp-inst per 6502 instruction, DRAM bytes per env-step)
+    ("k_interp_split", 32, 1, 3): (2808290676 / 600042217, (13156864 + 114785280) / 32768),
+    ("k_interp_split", 32, 1, 2): (417842913 / 94159103, (1275392 + 96768) / 4096),
 }
 # Algorithmic bytes of the fused rasterise + preprocess kernel per env-step,
 # besides 4 bytes per logged TIA write: snapshots and record counts of the two
@@ -57,8 +59,11 @@ INTERP_CAPTURES = {
 # ring, the 84x84x4 stack written out, the new plane written to the ring and
 # the ring head.
 FUSED_FIXED_BYTES_PER_ENV_STEP = 2 * 64 + 2 * 8 + 3 * 7056 + 4 * 7056 + 7056 + 1
+# Warp instructions per env-step of the fused kernel (it is bound by issue,
+# not HBM), from the same captures: smsp__inst_executed.sum / env-steps.
+FUSED_WARP_INST_PER_ENV_STEP = {3: 9062309897 / 32768, 2: 1302428699 / 4096}
 # DRAM bytes per env-step of the fused kernel, from an ncu capture per config.
-FUSED_DRAM_BYTES_PER_ENV_STEP = {}
+FUSED_DRAM_BYTES_PER_ENV_STEP = {3: (864005376 + 1107577000) / 32768, 2: (109952512 + 95163648) / 4096}
 
 
 def parse(argv=None):
@@ -83,6 +88,7 @@ def parse(argv=None):
     p.add_argument("--warps-per-frame", type=int, default=0)
     p.add_argument("--tia-warps", type=int, default=0, choices=[0, 1, 2])
     p.add_argument("--grouping", type=int, default=0, choices=[0, 1, 2])
+    p.add_argument("--dispatch", type=int, default=0, choices=[0, 1, 2])
     p.add_argument("--divergence", action="store_true",
                    help="divergence study: frames/s and lockstep lane efficiency per window of steps from one shared "
                         "start state per cartridge, beside a run from the usual random start states and the oracle "
@@ -376,6 +382,8 @@ def make_env(w, form, args, rank):
               raster_warps_per_frame=args.warps_per_frame, tia_warps=args.tia_warps)
     if args.grouping:
         kw["grouping"] = args.grouping
+    if args.dispatch:
+        kw["dispatch"] = args.dispatch
     # replicas: each rank runs the whole workload with its own env keys
     return AtariEnv([r.data for r in w.roms], [(r.score_addr, r.gameover_addr) for r in w.roms], w.env_rom,
                     luma=synth.luma_table(), env_key=replica_env_keys(w.n_envs, rank), frameskip=w.frameskip,
@@ -436,7 +444,7 @@ def profile_pass(env, do_step, acts, flush):
     return env.profile_read(), instr / k, logrec / k, rounds / k
 
 
-def interp_roofline(prof, instr_per_step, kernel, lanes, config, n_envs, frameskip):
+def interp_roofline(prof, instr_per_step, kernel, lanes, dispatch, config, n_envs, frameskip):
     """Issue-slot roofline of the interpreter (plain integer and control work:
     no tensor-core or FLOP peak applies)."""
     ms, n = prof.get("interpreter", (0.0, 0))
@@ -444,13 +452,13 @@ def interp_roofline(prof, instr_per_step, kernel, lanes, config, n_envs, framesk
         return None
     dur = ms / n / 1000.0
     peak = SM_COUNT * SMSP_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
-    cap = INTERP_CAPTURES.get((kernel, lanes, config))
-    src = f"ncu capture of {kernel}, {lanes} envs/warp, this workload"
+    cap = INTERP_CAPTURES.get((kernel, lanes, dispatch, config))
+    src = f"ncu capture of {kernel}, {lanes} envs/warp, dispatch {dispatch}, this workload"
     if cap is None:
-        other = [(k, v) for k, v in INTERP_CAPTURES.items() if k[0] == kernel and k[1] == lanes]
+        other = [(k, v) for k, v in INTERP_CAPTURES.items() if k[:3] == (kernel, lanes, dispatch)]
         if other:
             cap = other[0][1]
-            src = f"ncu capture of {kernel}, {lanes} envs/warp, workload config {other[0][0][2]}"
+            src = f"ncu capture of {kernel}, {lanes} envs/warp, dispatch {dispatch}, workload config {other[0][0][3]}"
     ach = cap[0] * instr_per_step / dur / 1e9 if cap else None
     return {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "Gwarp-inst/s",
             "frac": (ach / peak) if ach else None, "traffic": cap[1] * n_envs if cap else None,
@@ -473,10 +481,16 @@ def fused_roofline(prof, logrec_per_step, config, n_envs):
     peak = hbm if hbm else 6800.0
     ach = per_step * n_envs / dur / 1e9
     tb = FUSED_DRAM_BYTES_PER_ENV_STEP.get(config)
+    wi = FUSED_WARP_INST_PER_ENV_STEP.get(config)
+    issue_peak = SM_COUNT * SMSP_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
     return {"bound": "hbm", "kernel": "fused_raster_preprocess", "achieved": ach, "peak": peak, "unit": "GB/s",
             "frac": ach / peak, "traffic": tb * n_envs if tb else None, "algorithmic_bytes_per_env_step": per_step,
             "launch_ms": dur * 1000.0,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if hbm else "fallback 6.8 TB/s"}
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if hbm else "fallback 6.8 TB/s",
+            # what binds it in practice: issue slots (same method as the interpreter's roofline)
+            "issue": {"achieved": wi * n_envs / dur / 1e9 if wi else None, "peak": issue_peak,
+                      "unit": "Gwarp-inst/s", "frac": wi * n_envs / dur / 1e9 / issue_peak if wi else None,
+                      "warp_inst_per_env_step": wi}}
 
 
 def inference_run(args, rank, flush):
@@ -582,11 +596,18 @@ def divergence_run(args, w, rank):
             break
     return {"divergence": {
         "workload": w.name, "n_envs": w.n_envs, "window_steps": win, "steps": S,
-        "launch_shape": dict(zip(["envs_per_warp", "envs_per_block", "warps_per_frame", "grid", "tia_warps",
-                                  "grouping"], shape)),
+        "launch_shape": shape_dict(shape),
         "shared_start": shared, "random_start": random_start,
         "oracle_shared_start": {"envs": n, "cores": cores, "cpu_model": cpu_model(), "windows": oracle_curve},
         "l2": "flushed (256 MB write) before each step"}}
+
+
+def shape_dict(shape):
+    """launch_shape() as named fields (the grouping word also carries the
+    compact-dispatch flag, 4)."""
+    e, b, wpf, grid, tia, g = shape
+    return {"envs_per_warp": e, "envs_per_block": b, "warps_per_frame": wpf, "grid": grid, "tia_warps": tia,
+            "grouping": g & 3, "dispatch": 2 if g & 4 else 1}
 
 
 def kernel_name(env, form):
@@ -647,7 +668,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         if rank == 0:
             print(json.dumps({"capture": w.name, "kernel": kernel_name(env, args.form),
-                              "launch_shape": env.launch_shape(), "n_envs": w.n_envs,
+                              "launch_shape": shape_dict(env.launch_shape()), "n_envs": w.n_envs,
                               "m6502_inst_per_step": [c[0] for c in counts],
                               "tia_log_records_per_step": [c[1] for c in counts],
                               "lane_rounds_per_step": [c[2] for c in counts]}), flush=True)
@@ -683,7 +704,8 @@ def main(argv=None):
         dt = allreduce_max(time.perf_counter() - t0, ws)
         e2e = {"value": frames_all / dt, "unit": "frames/s", "h2d_bytes_per_step": int(ha[0].numel()),
                "d2h_bytes_per_step": int(ho.numel() + hr.numel() * 4 + hd.numel())}
-    roof = interp_roofline(prof, instr, kern, shape[0], args.config, w.n_envs, w.frameskip)
+    roof = interp_roofline(prof, instr, kern, shape[0], shape_dict(shape)["dispatch"], args.config, w.n_envs,
+                           w.frameskip)
     if roof and lane_rounds:
         # fraction of a warp's lanes executing per lockstep issue round
         roof["lockstep_lane_efficiency"] = instr / lane_rounds
@@ -732,8 +754,7 @@ def main(argv=None):
                        "sticky": bool(w.sticky),
                        "output": "84x84x4 uint8 stack" if w.output_mode == 1 else "210x160 palette frame",
                        "form": args.form, "l2": "flushed (256 MB write) before each timed step",
-                       "launch_shape": dict(zip(["envs_per_warp", "envs_per_block", "warps_per_frame", "grid",
-                                                 "tia_warps", "grouping"], shape)),
+                       "launch_shape": shape_dict(shape),
                        "parallelism": f"replicas x{ws}"},
             "plain": plain, "e2e": e2e, "roofline": roof, "roofline_fused": roof2, "kernels": kernels,
             "gpu_launches": gpu_launches, "m6502_inst_per_step": instr, "tia_log_records_per_step": logrec,

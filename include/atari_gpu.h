@@ -2,8 +2,8 @@
  * atari_gpu.h -- C ABI of the batched Atari 2600 emulator for GB300 (sm_103a).
  *
  * The library steps thousands of independent consoles (MOS 6507 CPU, TIA
- * video/collision chip, RIOT 6532 RAM/timer/ports, 2-16 KB cartridges with F8
- * and F6 bank switching) in lockstep on one GPU.  It is the data-parallel
+ * video/collision chip, RIOT 6532 RAM/timer/ports, 2-32 KB cartridges with
+ * F8, F6 and F4 bank switching) in lockstep on one GPU.  It is the data-parallel
  * emulation path of "Accelerating Reinforcement Learning through GPU Atari
  * Emulation" (CuLE), Section 3: a CPU-interpreter kernel that logs TIA
  * register writes to a per-env buffer in device memory, a TIA kernel that
@@ -93,7 +93,10 @@ typedef struct {
     int grouping;         /* batched form, how envs of one cartridge are ordered into warps: 1 = env order;
                              2 = bank-aware: re-sorted at every step by the bank their state holds at the
                              step's start (stable in env order), so a warp's lanes start in one bank of an
-                             F8/F6 cartridge; 0 = autotune */
+                             banked cartridge; 0 = autotune */
+    int dispatch;         /* batched form, the interpreter's hot opcode switch: 1 = every common opcode inline;
+                             2 = compact (indirect forms, BIT, stack pushes and pulls, indexed and absolute
+                             read-modify-writes through the general decoder: a smaller hot loop); 0 = autotune */
 } atari_config;
 
 /* Fill *cfg with the paper's defaults: F = 4, no sticky actions, 30 cached
@@ -103,7 +106,7 @@ ATARI_API void atari_default_config(atari_config *cfg);
 
 /*
  * Create n_envs environments.  roms[r] (host) holds rom_sizes[r] bytes:
- * 2048 or 4096 (plain, 2K mirrored), 8192 (F8) or 16384 (F6); other sizes
+ * 2048 or 4096 (plain, 2K mirrored), 8192 (F8), 16384 (F6) or 32768 (F4); other sizes
  * return ATARI_EINVAL.  env_rom[i] (host, n_envs) picks env i's cartridge;
  * env_key[i] (host, may be NULL = i) keys env i's random streams, so a
  * subset of envs created with the same keys reproduces the same run.
@@ -313,7 +316,8 @@ ATARI_API int atari_env_profile_read(atari_env *env, double *ms, uint64_t *launc
  * plain form: 32 envs per warp, 128 per block, 1 warp per frame, and the
  * grid of the interpreter launch).  tia_warps: 2 when paired TIA warps run
  * the envs' TIA side, else 1.  grouping: 1 env order, 2 bank-aware (see
- * atari_config; the plain form reports 1).  Host pointers; any may be NULL.
+ * atari_config; the plain form reports 1), plus 4 when the compact opcode
+ * switch is in use.  Host pointers; any may be NULL.
  * The paper runs one emulator per thread with no grouping (Section 3); the
  * shape is this library's own tuning and changes speed only, never results. */
 ATARI_API int atari_env_launch_shape(atari_env *env, int *envs_per_warp, int *envs_per_block,

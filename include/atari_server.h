@@ -61,6 +61,9 @@ typedef struct {
     uint64_t budget_bytes, bytes_in_use, fixed_bytes, per_env_bytes;
     int capacity;           /* env slots allocated on the device */
     int free_slots, queued_sessions, pending_requests;
+    uint64_t overlapped_ticks;  /* ticks whose device work began before an earlier tick's had ended
+                                   (CUDA events on the ticks' streams): continuous batching overlapping
+                                   on the GPU, not only queued on the host */
 } atari_server_stats;
 
 ATARI_API void atari_server_default_config(atari_server_config *c);

@@ -42,25 +42,27 @@ int fail(int code, const std::string &msg) {
   } while (0)
 
 // ------------------------------------------------------------------ decode table
-// The documented NMOS 6502 opcode matrix (row = high nibble, column = low
-// nibble); empty cells are undocumented opcodes, which halt the CPU.
+// The NMOS 6502 opcode matrix (row = high nibble, column = low nibble): the
+// documented opcodes and the 84 undocumented ones with a stable published
+// behaviour; empty cells (the 12 halting opcodes and ANE, LXA, SHA, SHX, SHY,
+// TAS, LAS, ARR) halt the CPU.
 const char *const OPMAP[256] = {
-    "BRK imp", "ORA izx", 0, 0, 0, "ORA zp", "ASL zp", 0, "PHP imp", "ORA imm", "ASL acc", 0, 0, "ORA abs", "ASL abs", 0,
-    "BPL rel", "ORA izy", 0, 0, 0, "ORA zpx", "ASL zpx", 0, "CLC imp", "ORA aby", 0, 0, 0, "ORA abx", "ASL abx", 0,
-    "JSR abs", "AND izx", 0, 0, "BIT zp", "AND zp", "ROL zp", 0, "PLP imp", "AND imm", "ROL acc", 0, "BIT abs", "AND abs", "ROL abs", 0,
-    "BMI rel", "AND izy", 0, 0, 0, "AND zpx", "ROL zpx", 0, "SEC imp", "AND aby", 0, 0, 0, "AND abx", "ROL abx", 0,
-    "RTI imp", "EOR izx", 0, 0, 0, "EOR zp", "LSR zp", 0, "PHA imp", "EOR imm", "LSR acc", 0, "JMP abs", "EOR abs", "LSR abs", 0,
-    "BVC rel", "EOR izy", 0, 0, 0, "EOR zpx", "LSR zpx", 0, "CLI imp", "EOR aby", 0, 0, 0, "EOR abx", "LSR abx", 0,
-    "RTS imp", "ADC izx", 0, 0, 0, "ADC zp", "ROR zp", 0, "PLA imp", "ADC imm", "ROR acc", 0, "JMP ind", "ADC abs", "ROR abs", 0,
-    "BVS rel", "ADC izy", 0, 0, 0, "ADC zpx", "ROR zpx", 0, "SEI imp", "ADC aby", 0, 0, 0, "ADC abx", "ROR abx", 0,
-    0, "STA izx", 0, 0, "STY zp", "STA zp", "STX zp", 0, "DEY imp", 0, "TXA imp", 0, "STY abs", "STA abs", "STX abs", 0,
-    "BCC rel", "STA izy", 0, 0, "STY zpx", "STA zpx", "STX zpy", 0, "TYA imp", "STA aby", "TXS imp", 0, 0, "STA abx", 0, 0,
-    "LDY imm", "LDA izx", "LDX imm", 0, "LDY zp", "LDA zp", "LDX zp", 0, "TAY imp", "LDA imm", "TAX imp", 0, "LDY abs", "LDA abs", "LDX abs", 0,
-    "BCS rel", "LDA izy", 0, 0, "LDY zpx", "LDA zpx", "LDX zpy", 0, "CLV imp", "LDA aby", "TSX imp", 0, "LDY abx", "LDA abx", "LDX aby", 0,
-    "CPY imm", "CMP izx", 0, 0, "CPY zp", "CMP zp", "DEC zp", 0, "INY imp", "CMP imm", "DEX imp", 0, "CPY abs", "CMP abs", "DEC abs", 0,
-    "BNE rel", "CMP izy", 0, 0, 0, "CMP zpx", "DEC zpx", 0, "CLD imp", "CMP aby", 0, 0, 0, "CMP abx", "DEC abx", 0,
-    "CPX imm", "SBC izx", 0, 0, "CPX zp", "SBC zp", "INC zp", 0, "INX imp", "SBC imm", "NOP imp", 0, "CPX abs", "SBC abs", "INC abs", 0,
-    "BEQ rel", "SBC izy", 0, 0, 0, "SBC zpx", "INC zpx", 0, "SED imp", "SBC aby", 0, 0, 0, "SBC abx", "INC abx", 0,
+    "BRK imp", "ORA izx", 0, "SLO izx", "NOP zp", "ORA zp", "ASL zp", "SLO zp", "PHP imp", "ORA imm", "ASL acc", "ANC imm", "NOP abs", "ORA abs", "ASL abs", "SLO abs",
+    "BPL rel", "ORA izy", 0, "SLO izy", "NOP zpx", "ORA zpx", "ASL zpx", "SLO zpx", "CLC imp", "ORA aby", "NOP imp", "SLO aby", "NOP abx", "ORA abx", "ASL abx", "SLO abx",
+    "JSR abs", "AND izx", 0, "RLA izx", "BIT zp", "AND zp", "ROL zp", "RLA zp", "PLP imp", "AND imm", "ROL acc", "ANC imm", "BIT abs", "AND abs", "ROL abs", "RLA abs",
+    "BMI rel", "AND izy", 0, "RLA izy", "NOP zpx", "AND zpx", "ROL zpx", "RLA zpx", "SEC imp", "AND aby", "NOP imp", "RLA aby", "NOP abx", "AND abx", "ROL abx", "RLA abx",
+    "RTI imp", "EOR izx", 0, "SRE izx", "NOP zp", "EOR zp", "LSR zp", "SRE zp", "PHA imp", "EOR imm", "LSR acc", "ALR imm", "JMP abs", "EOR abs", "LSR abs", "SRE abs",
+    "BVC rel", "EOR izy", 0, "SRE izy", "NOP zpx", "EOR zpx", "LSR zpx", "SRE zpx", "CLI imp", "EOR aby", "NOP imp", "SRE aby", "NOP abx", "EOR abx", "LSR abx", "SRE abx",
+    "RTS imp", "ADC izx", 0, "RRA izx", "NOP zp", "ADC zp", "ROR zp", "RRA zp", "PLA imp", "ADC imm", "ROR acc", 0, "JMP ind", "ADC abs", "ROR abs", "RRA abs",
+    "BVS rel", "ADC izy", 0, "RRA izy", "NOP zpx", "ADC zpx", "ROR zpx", "RRA zpx", "SEI imp", "ADC aby", "NOP imp", "RRA aby", "NOP abx", "ADC abx", "ROR abx", "RRA abx",
+    "NOP imm", "STA izx", "NOP imm", "SAX izx", "STY zp", "STA zp", "STX zp", "SAX zp", "DEY imp", "NOP imm", "TXA imp", 0, "STY abs", "STA abs", "STX abs", "SAX abs",
+    "BCC rel", "STA izy", 0, 0, "STY zpx", "STA zpx", "STX zpy", "SAX zpy", "TYA imp", "STA aby", "TXS imp", 0, 0, "STA abx", 0, 0,
+    "LDY imm", "LDA izx", "LDX imm", "LAX izx", "LDY zp", "LDA zp", "LDX zp", "LAX zp", "TAY imp", "LDA imm", "TAX imp", 0, "LDY abs", "LDA abs", "LDX abs", "LAX abs",
+    "BCS rel", "LDA izy", 0, "LAX izy", "LDY zpx", "LDA zpx", "LDX zpy", "LAX zpy", "CLV imp", "LDA aby", "TSX imp", 0, "LDY abx", "LDA abx", "LDX aby", "LAX aby",
+    "CPY imm", "CMP izx", "NOP imm", "DCP izx", "CPY zp", "CMP zp", "DEC zp", "DCP zp", "INY imp", "CMP imm", "DEX imp", "SBX imm", "CPY abs", "CMP abs", "DEC abs", "DCP abs",
+    "BNE rel", "CMP izy", 0, "DCP izy", "NOP zpx", "CMP zpx", "DEC zpx", "DCP zpx", "CLD imp", "CMP aby", "NOP imp", "DCP aby", "NOP abx", "CMP abx", "DEC abx", "DCP abx",
+    "CPX imm", "SBC izx", "NOP imm", "ISC izx", "CPX zp", "SBC zp", "INC zp", "ISC zp", "INX imp", "SBC imm", "NOP imp", "SBC imm", "CPX abs", "SBC abs", "INC abs", "ISC abs",
+    "BEQ rel", "SBC izy", 0, "ISC izy", "NOP zpx", "SBC zpx", "INC zpx", "ISC zpx", "SED imp", "SBC aby", "NOP imp", "ISC aby", "NOP abx", "SBC abx", "INC abx", "ISC abx",
 };
 
 const char *const MNEMONICS[] = {"JAM", "ADC", "AND", "ASL", "BCC", "BCS", "BEQ", "BIT", "BMI", "BNE", "BPL",
@@ -68,7 +70,8 @@ const char *const MNEMONICS[] = {"JAM", "ADC", "AND", "ASL", "BCC", "BCS", "BEQ"
                                  "DEX", "DEY", "EOR", "INC", "INX", "INY", "JMP", "JSR", "LDA", "LDX", "LDY",
                                  "LSR", "NOP", "ORA", "PHA", "PHP", "PLA", "PLP", "ROL", "ROR", "RTI", "RTS",
                                  "SBC", "SEC", "SED", "SEI", "STA", "STX", "STY", "TAX", "TAY", "TSX", "TXA",
-                                 "TXS", "TYA"};
+                                 "TXS", "TYA", "SLO", "RLA", "SRE", "RRA", "SAX", "LAX", "DCP", "ISC", "ANC",
+                                 "ALR", "SBX"};
 const char *const MODES[] = {"imp", "acc", "imm", "zp", "zpx", "zpy", "abs", "abx", "aby", "ind", "izx", "izy", "rel"};
 
 // Cycle counts from the documented timing rules of each instruction class.
@@ -83,7 +86,12 @@ uint32_t cycles_for(uint32_t op, uint32_t mode, bool &penalty) {
     default: break;
   }
   if (mode == REL || mode == IMP) return 2;
-  if (op == O_STA || op == O_STX || op == O_STY) {
+  if (op == O_SLO || op == O_RLA || op == O_SRE || op == O_RRA || op == O_DCP || op == O_ISC) {
+    switch (mode) {  // undocumented read-modify-write: always the long count
+      case ZP: return 5; case ZPX: case ABS: return 6; case ABX: case ABY: return 7; default: return 8;  // izx, izy
+    }
+  }
+  if (op == O_STA || op == O_STX || op == O_STY || op == O_SAX) {
     switch (mode) {
       case ZP: return 3; case ZPX: case ZPY: case ABS: return 4;
       case ABX: case ABY: return 5; default: return 6;  // izx, izy
@@ -101,8 +109,8 @@ uint32_t cycles_for(uint32_t op, uint32_t mode, bool &penalty) {
   }
 }
 
-// t[256] <- per opcode: operation | mode << 8 | base cycles << 12 | page-cross
-// penalty << 15; 0 for undocumented opcodes.
+// t[256] <- per opcode: operation | mode << 8 | base cycles << 12 (4 bits) |
+// page-cross penalty << 16; 0 for the opcodes that halt the CPU.
 void fill_decode_table(uint32_t *t) {
   for (int o = 0; o < 256; ++o) {
     t[o] = 0;
@@ -116,7 +124,7 @@ void fill_decode_table(uint32_t *t) {
       if (!strcmp(MODES[i], md)) mode = i;
     bool pen;
     uint32_t cyc = cycles_for(op, mode, pen);
-    t[o] = op | mode << 8 | cyc << 12 | (pen ? 1u : 0u) << 15;
+    t[o] = op | mode << 8 | cyc << 12 | (pen ? 1u : 0u) << 16;
   }
 }
 
@@ -136,7 +144,7 @@ uint32_t rom_info_word(size_t rom_size, const atari_rom_meta &meta) {
 }
 
 // ------------------------------------------------------------------ kernels
-constexpr int ROM_SLOT = 16384;  // bytes reserved per cartridge image on the device
+constexpr int ROM_SLOT = 32768;  // bytes reserved per cartridge image on the device (the largest, F4)
 
 struct RomInfo {
   uint32_t scheme, score, gameover;
@@ -481,7 +489,7 @@ struct atari_env {
   uint8_t *d_act = nullptr;   // staging for atari_env_step_host
   uint8_t *d_obs_tmp = nullptr;
   // batched form
-  uint8_t *d_romb = nullptr;        // [n_roms][16384] cartridge bytes for the batched stage
+  uint8_t *d_romb = nullptr;        // [n_roms][ROMB_SLOT] cartridge bytes for the batched stage
   uint8_t *d_dec_op = nullptr;      // 512 bytes
   int32_t *d_grp = nullptr;         // rom, start, count per work item (3 * n_groups) then perm (n)
   int32_t *d_seg = nullptr;         // first env-list position of each cartridge (n_roms + 1)
@@ -491,6 +499,7 @@ struct atari_env {
   int *d_queue = nullptr;
   int n_groups = 0, lanes = 32, warps = 4, wpf = 4, grid = 0, rom_stage = 4096, max_blocks = 1;
   bool split = false;   // paired CPU / TIA warps (k_interp_split)
+  bool compact = false; // the interpreter with the compact hot opcode switch
   std::vector<int32_t> h_env_rom;
   std::vector<uint32_t> h_banks;
   cudaStream_t cap_stream = nullptr;
@@ -509,6 +518,7 @@ int scheme_of(size_t sz) {
   if (sz == 2048 || sz == 4096) return 0;
   if (sz == 8192) return 1;
   if (sz == 16384) return 2;
+  if (sz == 32768) return 3;
   return -1;
 }
 
@@ -526,9 +536,9 @@ int validate(const atari_config &c) {
   if (c.sticky != 0 && c.sticky != 1) return fail(ATARI_EINVAL, "sticky must be 0 or 1");
   if (c.envs_per_block < 0 || c.envs_per_block > 128 || c.envs_per_warp < 0 || c.envs_per_warp > 32 ||
       c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4 || c.tia_warps < 0 || c.tia_warps > 3 ||
-      c.grouping < 0 || c.grouping > 2)
+      c.grouping < 0 || c.grouping > 2 || c.dispatch < 0 || c.dispatch > 2)
     return fail(ATARI_EINVAL, "envs_per_block must be 0..128, envs_per_warp 0..32, raster_warps_per_frame 0..4, "
-                              "tia_warps 0..3, grouping 0..2");
+                              "tia_warps 0..3, grouping 0..2, dispatch 0..2");
   return 0;
 }
 
@@ -580,11 +590,13 @@ int build_groups(atari_env *E, int lanes, int warps, bool split) {
   const size_t smem = (size_t)E->rom_stage + 16 + 512 + (size_t)lanes * warps * (ENV_SMEM + (split ? 4 * QSTRIDE : 0));
   int per_sm = 0;
   if (split) {
-    CUDA_TRY(cudaFuncSetAttribute(k_interp_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_split, 2 * warps * 32, smem));
+    CUDA_TRY(cudaFuncSetAttribute(k_interp_split<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaFuncSetAttribute(k_interp_split<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_split<false>, 2 * warps * 32, smem));
   } else {
-    CUDA_TRY(cudaFuncSetAttribute(k_interp_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched, warps * 32, smem));
+    CUDA_TRY(cudaFuncSetAttribute(k_interp_batched<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaFuncSetAttribute(k_interp_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_interp_batched<false>, warps * 32, smem));
   }
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, E->device));
@@ -638,8 +650,14 @@ size_t interp_smem(const atari_env *E) {
 }
 // The batched interpreter in the env's current form and shape.
 void launch_interp(atari_env *E, const BatchArgs &a, int grid, cudaStream_t s) {
-  if (E->split) k_interp_split<<<grid, 2 * E->warps * 32, interp_smem(E), s>>>(a);
-  else k_interp_batched<<<grid, E->warps * 32, interp_smem(E), s>>>(a);
+  const unsigned th = (E->split ? 2 : 1) * E->warps * 32;
+  if (E->split) {
+    if (E->compact) k_interp_split<true><<<grid, th, interp_smem(E), s>>>(a);
+    else k_interp_split<false><<<grid, th, interp_smem(E), s>>>(a);
+  } else {
+    if (E->compact) k_interp_batched<true><<<grid, th, interp_smem(E), s>>>(a);
+    else k_interp_batched<false><<<grid, th, interp_smem(E), s>>>(a);
+  }
 }
 
 size_t fused_smem() { return 2 * 210 * 160 + 128 + 7056; }
@@ -719,7 +737,7 @@ size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg) {
   b += n * 2 * (size_t)cfg->log_cap * 4;                  // log
   b += n * 2 * 64 + n * 2 * 2 * 4;                        // snapshots, meta
   if (cfg->form == ATARI_FORM_PLAIN) b += n * 2 * 210 * 160;   // frames (plain form only)
-  else b += (size_t)n_roms * 16384 + 512 + n * 8 + 64 + (size_t)(n_roms + 1) * 4;  // stage bytes, work items, regrouping
+  else b += (size_t)n_roms * ROMB_SLOT + 512 + n * 8 + 64 + (size_t)(n_roms + 1) * 4;  // stage bytes, work items, regrouping
   if (cfg->output_mode == ATARI_OUT_STACK) b += n * 4 * 7056 + n;
   if (cfg->output_mode == ATARI_OUT_STACK && cfg->form == ATARI_FORM_BATCHED) b += n * 2 * 3 * 64;  // band snapshots
   b += n * (4 + 1 + 12 + 1);                              // rewards, dones, counters, action staging
@@ -739,7 +757,7 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
   if (cfg->output_mode == ATARI_OUT_STACK && !luma) return fail(ATARI_EINVAL, "luma table required for stack output");
   for (int r = 0; r < n_roms; ++r) {
     if (!roms[r] || scheme_of(rom_sizes[r]) < 0)
-      return fail(ATARI_EINVAL, "ROM " + std::to_string(r) + ": size must be 2048, 4096, 8192 or 16384");
+      return fail(ATARI_EINVAL, "ROM " + std::to_string(r) + ": size must be 2048, 4096, 8192, 16384 or 32768");
     if (meta[r].score_addr < 0x80 || meta[r].gameover_addr < 0x80)
       return fail(ATARI_EINVAL, "ROM " + std::to_string(r) + ": score/game-over addresses must be in $80-$FF");
   }
@@ -1072,6 +1090,31 @@ int autotune(atari_env *E) {
     }
     E->grouping = tg[2] < 0.97f * tg[1] ? 2 : 1;
   }
+  // opcode dispatch on the chosen shape and grouping: the full hot switch, or
+  // the compact one (rare forms through the general decoder); the compact
+  // switch must be 3 % faster to be taken
+  E->compact = E->cfg.dispatch == 2;
+  if (!rc && E->cfg.dispatch == 0) {
+    float td[2] = {0, 0};
+    for (int cmp = 0; cmp <= 1 && !rc; ++cmp) {
+      E->compact = cmp != 0;
+      BatchArgs a = batch_args(E, E->d_act, nullptr, nullptr);
+      for (int rep = 0; rep < 2; ++rep) {
+        if (cudaMemcpy(E->d_state, st_bak, n * 256, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+            cudaMemset(E->d_queue, 0, sizeof(int)) != cudaSuccess) {
+          rc = fail(ATARI_ECUDA, "autotune: state restore failed");
+          break;
+        }
+        cudaEventRecord(e0);
+        if (E->grouping == 2) launch_regroup(E, nullptr);
+        launch_interp(E, a, E->grid, nullptr);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&td[cmp], e0, e1);
+      }
+    }
+    E->compact = td[1] < 0.97f * td[0];
+  }
   if (!rc && E->cfg.output_mode == ATARI_OUT_STACK) {
     if (!(rc = dalloc(&ring_bak, n * 4 * 7056, dummy)) && !(rc = dalloc(&head_bak, n, dummy))) {
       cudaMemcpy(ring_bak, E->d_ring, n * 4 * 7056, cudaMemcpyDeviceToDevice);
@@ -1108,21 +1151,19 @@ int autotune(atari_env *E) {
 
 int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vector<uint32_t> &dec) {
   const int R = E->n_roms;
-  std::vector<uint8_t> bytes((size_t)R * 16384, 0u);
+  std::vector<uint8_t> bytes((size_t)R * ROMB_SLOT, 0u);
   std::vector<uint8_t> dec_op(512, 0);
-  auto info_of = [&](uint32_t opc) {
-    uint32_t t = dec[opc];
-    return ((t >> 8) & 0xFu) | ((t >> 12) & 7u) << 4 | ((t >> 15) & 1u) << 7;
-  };
+  // per opcode: operation | page-cross penalty << 7, then mode | cycles << 4
   for (int o = 0; o < 256; ++o) {
-    dec_op[o] = (uint8_t)(dec[o] & 0xFF);
-    dec_op[256 + o] = (uint8_t)info_of((uint32_t)o);
+    const uint32_t t = dec[o];
+    dec_op[o] = (uint8_t)((t & 0x7F) | ((t >> 16) & 1u) << 7);
+    dec_op[256 + o] = (uint8_t)(((t >> 8) & 0xFu) | ((t >> 12) & 0xFu) << 4);
   }
   uint32_t max_banks = 1;
   for (int r = 0; r < R; ++r) {
     const uint32_t banks = E->h_banks[r];
     max_banks = std::max(max_banks, banks);
-    memcpy(bytes.data() + (size_t)r * 16384, img.data() + (size_t)r * ROM_SLOT, (size_t)banks * 4096);
+    memcpy(bytes.data() + (size_t)r * ROMB_SLOT, img.data() + (size_t)r * ROM_SLOT, (size_t)banks * 4096);
   }
   E->rom_stage = (int)max_banks * 4096;
   E->banked = max_banks > 1;
@@ -1141,9 +1182,11 @@ int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vect
     int L = std::min(32, c.envs_per_warp), W = std::max(1, std::min(4, c.envs_per_block / L));
     E->wpf = c.raster_warps_per_frame > 0 ? c.raster_warps_per_frame : 4;
     E->grouping = c.grouping ? c.grouping : 1;
+    E->compact = c.dispatch == 2;
     return build_groups(E, L, W, c.tia_warps >= 2);
   }
   E->grouping = c.grouping ? c.grouping : 1;
+  E->compact = c.dispatch == 2;
   if (E->n == 0) return build_groups(E, 32, 4, c.tia_warps >= 2);
   return autotune(E);
 }
@@ -1372,7 +1415,7 @@ int atari_env_launch_shape(atari_env *E, int *envs_per_warp, int *envs_per_block
   if (raster_warps_per_frame) *raster_warps_per_frame = b ? E->wpf : 1;
   if (grid) *grid = b ? E->grid : (E->n + 127) / 128;
   if (tia_warps) *tia_warps = (b && E->split) ? 2 : 1;
-  if (grouping) *grouping = b ? E->grouping : 1;
+  if (grouping) *grouping = b ? (E->grouping | (E->compact ? 4 : 0)) : 1;
   return 0;
 }
 
@@ -1458,7 +1501,7 @@ extern "C" int atari_step_noalloc(const uint8_t *rom, size_t rom_size, atari_rom
     return fail(ATARI_EINVAL, "atari_step_noalloc: n_envs must be in 0.." + std::to_string(NA_MAX_ENVS) +
                                   " (the fixed scratch array holds at most that many envs)");
   const int sc = scheme_of(rom_size);
-  if (!rom || sc < 0) return fail(ATARI_EINVAL, "atari_step_noalloc: ROM size must be 2048, 4096, 8192 or 16384");
+  if (!rom || sc < 0) return fail(ATARI_EINVAL, "atari_step_noalloc: ROM size must be 2048, 4096, 8192, 16384 or 32768");
   if (meta.score_addr < 0x80 || meta.gameover_addr < 0x80)
     return fail(ATARI_EINVAL, "atari_step_noalloc: score/game-over addresses must be in $80-$FF");
   if (n_cache < 1 || n_cache > 64) return fail(ATARI_EINVAL, "atari_step_noalloc: n_cache must be in 1..64");

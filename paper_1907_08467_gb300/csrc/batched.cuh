@@ -25,7 +25,7 @@ namespace atari {
 struct BatchArgs {
   uint8_t *state;
   const uint8_t *cache;
-  const uint8_t *romb;       // [n_roms][16384] cartridge bytes, banks of 4096
+  const uint8_t *romb;       // [n_roms][ROMB_SLOT] cartridge bytes, banks of 4096
   const uint32_t *info;      // per ROM: scheme | score << 8 | gameover << 16 | banks << 24
   const uint8_t *dec_op;     // 512 bytes: op per opcode, then mode/cycles/penalty per opcode
   const uint8_t *actions;
@@ -66,8 +66,8 @@ __device__ __forceinline__ void fast_reset_from_cache(uint8_t *st, const uint8_t
 // Env slot i; o = where its action is read and its reward and done written.
 // Split form: logged-frame setup, frame records and the log count happen on
 // the TIA side, in queue order; the step ends once the TIA side has caught up.
-template <bool SPLIT>
-__device__ __forceinline__ void fast_step_env(FastConsoleT<SPLIT> &m, uint8_t *st, int i, int o, const BatchArgs &a,
+template <bool SPLIT, bool COMPACT>
+__device__ __forceinline__ void fast_step_env(FastConsoleT<SPLIT, COMPACT> &m, uint8_t *st, int i, int o, const BatchArgs &a,
                                               uint32_t rom, uint32_t score, uint32_t gameover) {
   const uint32_t *ew = reinterpret_cast<const uint32_t *>(st + S::EPISODE);
   uint32_t episode = ew[0], step_no = ew[1], env_key = ew[2], env_status = ew[3];
@@ -149,17 +149,20 @@ __device__ void tia_worker(IoCtx c, const uint32_t *q, int i, const BatchArgs &a
   if (a.tia_off) return;
   volatile uint32_t *vw = reinterpret_cast<volatile uint32_t *>(c.w());
   const volatile uint32_t *vq = reinterpret_cast<const volatile uint32_t *>(q);
-  uint32_t head = 0, ack = 0, lines = 0, log_total = 0, spins = 0;
+  uint32_t head = 0, ack = 0, lines = 0, log_total = 0;
+  uint64_t idle_since = 0;  // global-timer time the queue was first seen empty (0: not idle)
   for (;;) {
     if (head == vw[IO_QTAIL]) {
-      if (++spins > SPIN_LIMIT) {
+      const uint64_t now = global_ns();
+      if (!idle_since) idle_since = now;
+      else if (now - idle_since >= WAIT_NS) {
         c.Sset(IO_STATUS, c.G(IO_STATUS) | ST_STALL);
         break;
       }
       __nanosleep(128);  // an idle TIA lane polls gently: the CPU warps share the SM's memory pipe
       continue;
     }
-    spins = 0;
+    idle_since = 0;
     __threadfence_block();
     const uint32_t ev = vq[head & (QLEN - 1)];
     vw[IO_QHEAD] = ++head;
@@ -197,12 +200,13 @@ __device__ void tia_worker(IoCtx c, const uint32_t *q, int i, const BatchArgs &a
   }
 }
 
+template <bool COMPACT>
 __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t *rom8 = smem;                                  // rom_stage bytes, then 16 of padding
   uint8_t *dec_op = smem + (size_t)a.rom_stage + 16;
-  uint32_t *ram = reinterpret_cast<uint32_t *>(dec_op + 512);
-  uint32_t *iow = ram + RAM_STRIDE * a.E;
+  uint8_t *ram = dec_op + 512;
+  uint32_t *iow = reinterpret_cast<uint32_t *>(ram + RAM_BYTES * a.E);
   uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_STRIDE * a.E);
   __shared__ int s_group;
   for (int t = threadIdx.x; t < 512; t += blockDim.x) dec_op[t] = a.dec_op[t];
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
     const int rom = a.grp_rom[g];
     if (rom != cur_rom) {
       const uint32_t banks = a.info[rom] >> 24;
-      const uint4 *src = reinterpret_cast<const uint4 *>(a.romb + (size_t)rom * 16384);
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.romb + (size_t)rom * ROMB_SLOT);
       uint4 *dst = reinterpret_cast<uint4 *>(rom8);
       for (uint32_t q = threadIdx.x; q < banks * 256u; q += blockDim.x) dst[q] = src[q];
       if (threadIdx.x == 0) dst[banks * 256u] = make_uint4(0, 0, 0, 0);
@@ -235,10 +239,10 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
         const int o = a.opos ? a.opos[p] : i;
         uint8_t *st = a.state + (size_t)i * 256;
         const uint32_t inf = a.info[rom];
-        FastConsole m;
+        FastConsoleT<false, COMPACT> m;
         m.rom8 = rom8;
         m.dec_op = dec_op;
-        m.ram = ram + RAM_STRIDE * j;
+        m.ram = ram + RAM_BYTES * j;
         m.io = IoCtx{tia + TIA_STRIDE * j, iow + IO_STRIDE * j};
         m.scheme = inf & 0xFF;
         m.wmask = wmask;
@@ -253,12 +257,13 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
 // item's envs, warp W + w the TIA side of CPU warp w's envs (lane for lane).
 // Shared memory: cartridge stage, decoder table, per-env RAM, I/O words, TIA
 // file, then the per-env event queues.
-__global__ void __launch_bounds__(256, 1) k_interp_split(BatchArgs a) {
+template <bool COMPACT>
+__global__ void __launch_bounds__(256, 2) k_interp_split(BatchArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t *rom8 = smem;
   uint8_t *dec_op = smem + (size_t)a.rom_stage + 16;
-  uint32_t *ram = reinterpret_cast<uint32_t *>(dec_op + 512);
-  uint32_t *iow = ram + RAM_STRIDE * a.E;
+  uint8_t *ram = dec_op + 512;
+  uint32_t *iow = reinterpret_cast<uint32_t *>(ram + RAM_BYTES * a.E);
   uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_STRIDE * a.E);
   uint32_t *qs = reinterpret_cast<uint32_t *>(tia + TIA_STRIDE * a.E);
   __shared__ int s_group;
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_split(BatchArgs a) {
     const int rom = a.grp_rom[g];
     if (rom != cur_rom) {
       const uint32_t banks = a.info[rom] >> 24;
-      const uint4 *src = reinterpret_cast<const uint4 *>(a.romb + (size_t)rom * 16384);
+      const uint4 *src = reinterpret_cast<const uint4 *>(a.romb + (size_t)rom * ROMB_SLOT);
       uint4 *dst = reinterpret_cast<uint4 *>(rom8);
       for (uint32_t q = threadIdx.x; q < banks * 256u; q += blockDim.x) dst[q] = src[q];
       if (threadIdx.x == 0) dst[banks * 256u] = make_uint4(0, 0, 0, 0);
@@ -294,11 +299,11 @@ __global__ void __launch_bounds__(256, 1) k_interp_split(BatchArgs a) {
     const uint32_t inf = a.info[rom];
     const IoCtx io{tia + TIA_STRIDE * jj, iow + IO_STRIDE * jj};
     uint32_t *q = qs + QSTRIDE * jj;
-    FastConsoleT<true> m;
+    FastConsoleT<true, COMPACT> m;
     if (cpu && runs) {
       m.rom8 = rom8;
       m.dec_op = dec_op;
-      m.ram = ram + RAM_STRIDE * jj;
+      m.ram = ram + RAM_BYTES * jj;
       m.io = io;
       m.q = q;
       m.scheme = inf & 0xFF;
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_split(BatchArgs a) {
     }
     __syncthreads();  // the envs' state is in shared memory before the TIA side starts
     if (runs) {
-      if (cpu) fast_step_env<true>(m, st, i, o, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
+      if (cpu) fast_step_env<true, COMPACT>(m, st, i, o, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
       else tia_worker(io, q, i, a);
     }
   }
@@ -317,10 +322,11 @@ __global__ void __launch_bounds__(256, 1) k_interp_split(BatchArgs a) {
 // env list, envs are ordered by the bank their canonical state holds at the
 // start of the step (byte 5, reduced to the cartridge's bank bits), stable in
 // env order, so the lanes of a warp start the step in one bank.  A counting
-// sort with four keys; one block of 256 threads per cartridge.  Cartridges
-// with one bank keep the list as it is.
+// sort with up to eight keys (F4); one block of 256 threads per cartridge.
+// Cartridges with one bank keep the list as it is.
 __global__ void __launch_bounds__(256) k_group_by_bank(const uint8_t *state, const int32_t *perm_in,
                                                         const int32_t *seg, const uint32_t *info, int32_t *perm_out) {
+  constexpr uint32_t KEYS = 8;
   const int r = blockIdx.x;
   const int a = seg[r], b = seg[r + 1];
   const uint32_t banks = info[r] >> 24;
@@ -328,16 +334,16 @@ __global__ void __launch_bounds__(256) k_group_by_bank(const uint8_t *state, con
     for (int p = a + (int)threadIdx.x; p < b; p += blockDim.x) perm_out[p] = perm_in[p];
     return;
   }
-  const uint32_t mask = banks - 1;  // 1 for F8, 3 for F6
-  __shared__ int cnt[4], base[4], wcnt[8][4];
-  if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+  const uint32_t mask = banks - 1;  // 1 for F8, 3 for F6, 7 for F4
+  __shared__ int cnt[KEYS], base[KEYS], wcnt[8][KEYS];
+  if (threadIdx.x < KEYS) cnt[threadIdx.x] = 0;
   __syncthreads();
   for (int p = a + (int)threadIdx.x; p < b; p += blockDim.x)
     atomicAdd(&cnt[state[(size_t)perm_in[p] * 256 + 5] & mask], 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     int s = a;
-    for (int v = 0; v < 4; ++v) { base[v] = s; s += cnt[v]; }
+    for (uint32_t v = 0; v < KEYS; ++v) { base[v] = s; s += cnt[v]; }
   }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(256) k_group_by_bank(const uint8_t *state, con
     const uint32_t bk = valid ? (state[(size_t)env * 256 + 5] & mask) : 0u;
     uint32_t rank = 0;
 #pragma unroll
-    for (uint32_t v = 0; v < 4; ++v) {
+    for (uint32_t v = 0; v < KEYS; ++v) {
       const uint32_t m = __ballot_sync(0xFFFFFFFFu, valid && bk == v);
       if (lane == 0) wcnt[warp][v] = __popc(m);
       if (valid && bk == v) rank = __popc(m & ((1u << lane) - 1u));
@@ -360,7 +366,7 @@ __global__ void __launch_bounds__(256) k_group_by_bank(const uint8_t *state, con
       perm_out[base[bk] + off + (int)rank] = env;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < KEYS) {
       int t = 0;
       for (int w2 = 0; w2 < 8; ++w2) t += wcnt[w2][threadIdx.x];
       base[threadIdx.x] += t;
@@ -425,7 +431,7 @@ __device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uin
 
 // One block per env: warps [0, W) render frame F-1, warps [W, 2W) frame F,
 // each warp a band of rows; then luma max, 84x84 area resampling, stack push.
-__global__ void __launch_bounds__(256) k_raster_preprocess(const uint32_t *log, const uint8_t *snap, const uint8_t *bsnap,
+__global__ void __launch_bounds__(256, 3) k_raster_preprocess(const uint32_t *log, const uint8_t *snap, const uint8_t *bsnap,
                                                            const uint32_t *meta,
                                                            const uint8_t *luma_g, uint8_t *ring, uint8_t *head,
                                                            const uint8_t *done, uint8_t *obs, int n, int log_cap,

@@ -40,14 +40,16 @@ constexpr uint32_t ST_ILLEGAL = 1u, ST_FRAME_CAP = 2u, ST_LOG_OVERFLOW = 4u, ST_
 constexpr uint64_t NO_LINE = ~0ull;
 constexpr int WINDOW_Y0 = 31, FRAME_H = 210, FRAME_W = 160, CAP_LINES = 400;
 
-// Decode word: op | mode << 8 | cycles << 12 | read-penalty << 15
+// Decode word: op | mode << 8 | cycles << 12 (4 bits) | read-penalty << 16
 enum Mode : uint32_t { IMP, ACC, IMM, ZP, ZPX, ZPY, ABS, ABX, ABY, IND, IZX, IZY, REL };
 enum Op : uint32_t {
   O_JAM = 0, O_ADC, O_AND, O_ASL, O_BCC, O_BCS, O_BEQ, O_BIT, O_BMI, O_BNE, O_BPL, O_BRK, O_BVC,
   O_BVS, O_CLC, O_CLD, O_CLI, O_CLV, O_CMP, O_CPX, O_CPY, O_DEC, O_DEX, O_DEY, O_EOR, O_INC,
   O_INX, O_INY, O_JMP, O_JSR, O_LDA, O_LDX, O_LDY, O_LSR, O_NOP, O_ORA, O_PHA, O_PHP, O_PLA,
   O_PLP, O_ROL, O_ROR, O_RTI, O_RTS, O_SBC, O_SEC, O_SED, O_SEI, O_STA, O_STX, O_STY, O_TAX,
-  O_TAY, O_TSX, O_TXA, O_TXS, O_TYA
+  O_TAY, O_TSX, O_TXA, O_TXS, O_TYA,
+  // undocumented NMOS operations with a stable published behaviour
+  O_SLO, O_RLA, O_SRE, O_RRA, O_SAX, O_LAX, O_DCP, O_ISC, O_ANC, O_ALR, O_SBX
 };
 
 // TIA write registers that change what collides, and those the replay needs.
@@ -249,7 +251,7 @@ struct Console {
   __device__ void load(const uint8_t *s) {
     // the cartridge latches only its own bank bits (F8 one, F6 two); scheme is set before load
     A = s[S::A]; X = s[S::X]; Y = s[S::Y]; SP = s[S::SP]; P = s[S::P];
-    bank = s[S::BANK] & (scheme == 2 ? 3u : scheme == 1 ? 1u : 0u);
+    bank = s[S::BANK] & (scheme == 3 ? 7u : scheme == 2 ? 3u : scheme == 1 ? 1u : 0u);
     PC = s[S::PC] | (uint32_t)s[S::PC + 1] << 8;
     uint64_t k = ld64(s + S::CYCLES);
     tim_cw = ld64(s + S::TIM_CW);
@@ -550,6 +552,7 @@ struct Console {
   __device__ __forceinline__ void hotspot(uint32_t off) {
     if (scheme == 1) { if (off == 0xFF8 || off == 0xFF9) bank = off - 0xFF8; }
     else if (scheme == 2) { if (off >= 0xFF6 && off <= 0xFF9) bank = off - 0xFF6; }
+    else if (scheme == 3) { if (off >= 0xFF4 && off <= 0xFFB) bank = off - 0xFF4; }
   }
   __device__ __forceinline__ uint32_t rd(uint32_t addr, uint32_t t) {
     addr &= 0x1FFF;
@@ -632,7 +635,7 @@ struct Console {
     const uint32_t opcode = rd(pc, k0);
     const uint32_t d = dec[opcode];
     const uint32_t op = d & 0xFF, mode = (d >> 8) & 0xF;
-    uint32_t n = (d >> 12) & 7;
+    uint32_t n = (d >> 12) & 15;
     if (op == O_JAM) { jam = 1; status |= ST_ILLEGAL; return; }
     uint32_t b1 = 0, b2 = 0, ea = 0, cross = 0;
     switch (mode) {
@@ -655,7 +658,7 @@ struct Console {
                   uint32_t b = lo | hi << 8; ea = (b + Y) & 0xFFFF; cross = (b ^ ea) >> 8; PC = (pc + 2) & 0xFFFF; break; }
       case REL: b1 = rd(pc + 1, k0); PC = (pc + 2) & 0xFFFF; ea = (PC + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF; break;
     }
-    if (cross && (d >> 15)) n++;
+    if (cross && ((d >> 16) & 1)) n++;
     instret++;
     if (mode == REL) {
       uint32_t take;
@@ -710,6 +713,36 @@ struct Console {
         else { wr(ea, old, kA - 1); wr(ea, r, kA); }
         break;
       }
+      case O_SLO: case O_RLA: case O_SRE: case O_RRA: case O_DCP: case O_ISC: {
+        // read-modify-write of memory (both writes), then the accumulator operation
+        const uint32_t old = rd(ea, kA - 2);
+        uint32_t r, c = P & 1u;
+        switch (op) {
+          case O_SLO: r = (old << 1) & 0xFF; c = old >> 7; break;
+          case O_RLA: r = ((old << 1) | (P & 1u)) & 0xFF; c = old >> 7; break;
+          case O_SRE: r = old >> 1; c = old & 1; break;
+          case O_RRA: r = (old >> 1) | ((P & 1u) << 7); c = old & 1; break;
+          case O_DCP: r = (old - 1) & 0xFF; break;
+          default: r = (old + 1) & 0xFF; break;
+        }
+        wr(ea, old, kA - 1);
+        wr(ea, r, kA);
+        switch (op) {
+          case O_SLO: A |= r; P = (P & ~1u) | c; nz(A); break;
+          case O_RLA: A &= r; P = (P & ~1u) | c; nz(A); break;
+          case O_SRE: A ^= r; P = (P & ~1u) | c; nz(A); break;
+          case O_RRA: P = (P & ~1u) | c; adc(r); break;
+          case O_DCP: cmp(A, r); break;
+          default: sbc(r); break;
+        }
+        break;
+      }
+      case O_SAX: wr(ea, A & X, kA); break;
+      case O_LAX: A = rd(ea, kA); X = A; nz(A); break;
+      case O_ANC: A &= b1; nz(A); P = (P & ~1u) | (A >> 7); break;
+      case O_ALR: A &= b1; P = (P & ~1u) | (A & 1u); A >>= 1; nz(A); break;
+      case O_SBX: { const uint32_t ax = A & X; P = (P & ~1u) | (ax >= b1 ? 1u : 0u); X = (ax - b1) & 0xFF; nz(X); break; }
+      case O_NOP: if (mode != IMP && mode != IMM) (void)rd(ea, kA); break;  // the operand read
       case O_INX: X = (X + 1) & 0xFF; nz(X); break;
       case O_INY: Y = (Y + 1) & 0xFF; nz(Y); break;
       case O_DEX: X = (X - 1) & 0xFF; nz(X); break;
@@ -743,7 +776,7 @@ struct Console {
         PC = lo | hi << 8;
         break;
       }
-      default: break;  // NOP
+      default: break;
     }
     uint32_t k = k0 + n;
     if (wsync) k = ((k + 75u) / 76u) * 76u;

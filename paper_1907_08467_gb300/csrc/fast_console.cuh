@@ -5,11 +5,11 @@
 //     addressing mode and cycle count folded in;
 //   - CPU registers (flags split, N and Z kept as the last result byte),
 //     the cycle counter and the bank in registers;
-//   - RAM (one 32-bit word per byte), the TIA register file (bytes) and the
-//     I/O state (collision cursor and latches, RIOT timer and ports, inputs,
-//     log cursor, frame base line) in shared memory, one block per env with
-//     odd word strides, so lanes reading the same field never bank-conflict
-//     and every access is a base pointer plus an offset;
+//   - RAM (bytes), the TIA register file (bytes) and the I/O state
+//     (collision cursor and latches, RIOT timer and ports, inputs, log
+//     cursor, frame base line) in shared memory, one block per env with odd
+//     word strides, so lanes reading the same field never bank-conflict and
+//     every access is a base pointer plus an offset;
 //   - the block's cartridge staged in shared memory as bytes (16 KB for an
 //     F6 cartridge); an instruction's bytes are fetched as two aligned words
 //     joined by one funnel shift.
@@ -42,12 +42,17 @@ constexpr uint32_t IO_WSYNC = 1u, IO_VSYNC_RISE = 2u;
 
 
 // Per-env blocks of shared memory, env-major, with strides chosen so that a
-// warp's lanes touching the same field hit 32 different banks: RAM one word
-// per byte (129 words per env), I/O state 19 words, TIA file 44 bytes (11
-// words).  Every access is the lane's base plus a constant or one add.
-constexpr uint32_t RAM_STRIDE = 129, IO_STRIDE = IO_WORDS, TIA_STRIDE = 44;
-static_assert(IO_STRIDE % 2 == 1 && (TIA_STRIDE / 4) % 2 == 1 && RAM_STRIDE % 2 == 1, "odd word strides");
-constexpr uint32_t ENV_SMEM = 4 * RAM_STRIDE + 4 * IO_STRIDE + TIA_STRIDE;
+// warp's lanes touching the same field hit 32 different banks: RAM 128 bytes
+// padded to 132 (33 words), I/O state IO_WORDS words, TIA file 44 bytes (11
+// words).  Every access is the lane's base plus a constant or one add.  Bytes
+// rather than one word per RAM byte keep a 64-env work item small enough for
+// four blocks per SM.
+constexpr uint32_t RAM_BYTES = 132, IO_STRIDE = IO_WORDS, TIA_STRIDE = 44;
+static_assert(IO_STRIDE % 2 == 1 && (TIA_STRIDE / 4) % 2 == 1 && (RAM_BYTES / 4) % 2 == 1 && RAM_BYTES % 4 == 0,
+              "odd word strides");
+constexpr uint32_t ENV_SMEM = RAM_BYTES + 4 * IO_STRIDE + TIA_STRIDE;
+// bytes per cartridge in the batched form's device copy (up to eight 4 KB banks, F4)
+constexpr uint32_t ROMB_SLOT = 32768;
 
 // Shared-memory views of one env's TIA file and I/O state.  The pointers
 // reach the out-of-line I/O functions as plain pointers; the assumption lets
@@ -363,8 +368,16 @@ constexpr uint32_t QSTRIDE = QLEN + 1;    // shared-memory words per env queue (
 constexpr uint32_t EV_WRITE = 0u, EV_FRAME_END = 1u << 30, EV_CTRL = 2u << 30;
 constexpr uint32_t EV_BEGIN_LOG = EV_CTRL, EV_END_LOG = EV_CTRL | 1u << 28, EV_SYNC = EV_CTRL | 2u << 28,
                    EV_STEP_END = EV_CTRL | 3u << 28;
-constexpr uint32_t SPIN_LIMIT = 1u << 20;  // polls (each after a short sleep) before the env is declared stalled;
-                                           // far above the longest legitimate wait, about a frame of the partner
+// A wait between an env's CPU and TIA warps gives up after WAIT_NS of the
+// GPU's global timer and the env is declared stalled.  The longest legitimate
+// wait is about one frame of the slowest lane of the partner warp (a few
+// milliseconds), so the limit is far above it and still short.
+constexpr uint64_t WAIT_NS = 200000000ull;  // 200 ms
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // registers whose writes reach the TIA side (WSYNC, RSYNC, audio and unused
 // addresses change nothing there)
 constexpr uint64_t SPLIT_PUSH_REGS = LOG_REGS | COLL_REGS | 1ull | (1ull << 0x2C);
@@ -378,7 +391,9 @@ __device__ __noinline__ uint32_t fc_q_wait_room(uint32_t *iow, uint32_t qtail) {
   __builtin_assume(__isShared(iow));
   const volatile uint32_t *h = iow + IO_QHEAD;
   uint32_t head = *h;
-  for (uint32_t spins = 0; qtail - head >= QLEN && spins < SPIN_LIMIT; ++spins) {
+  if (qtail - head < QLEN) return head;
+  const uint64_t t0 = global_ns();
+  while (qtail - head >= QLEN && global_ns() - t0 < WAIT_NS) {
     __nanosleep(32);
     head = *h;
   }
@@ -387,8 +402,10 @@ __device__ __noinline__ uint32_t fc_q_wait_room(uint32_t *iow, uint32_t qtail) {
 __device__ __noinline__ bool fc_q_wait_ack(uint32_t *iow, uint32_t n) {
   __builtin_assume(__isShared(iow));
   const volatile uint32_t *a = iow + IO_ACK;
-  for (uint32_t spins = 0; (int32_t)(*a - n) < 0; ++spins) {
-    if (spins >= SPIN_LIMIT) return false;
+  if ((int32_t)(*a - n) >= 0) return true;
+  const uint64_t t0 = global_ns();
+  while ((int32_t)(*a - n) < 0) {
+    if (global_ns() - t0 >= WAIT_NS) return false;
     __nanosleep(32);
   }
   return true;
@@ -428,14 +445,20 @@ __device__ __noinline__ uint32_t fc_split_io_read(IoCtx c, uint32_t *q, uint32_t
   return SIO_PUSHED | fc_cx_byte(vw[IO_CX], reg);
 }
 
-template <bool SPLIT> struct FastConsoleT;
-template <bool SPLIT> __device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT> *self);
+// COMPACT: the hot opcode switch keeps only the common addressing forms
+// (implied, accumulator, immediate, zero page and absolute reads, writes and
+// branches, indexed loads and stores); the indirect forms, BIT, stack
+// pushes and pulls and indexed or absolute read-modify-writes go to the
+// general decoder.  A smaller hot loop for the instruction cache; the
+// results are the same either way.
+template <bool SPLIT, bool COMPACT = false> struct FastConsoleT;
+template <bool SPLIT, bool COMPACT> __device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT, COMPACT> *self);
 
-template <bool SPLIT>
+template <bool SPLIT, bool COMPACT>
 struct FastConsoleT {
   const uint8_t *rom8;     // staged cartridge bytes (banks of 4096, then 16 bytes of padding)
-  const uint8_t *dec_op;   // general decoder: opcode -> operation, then mode/cycles/penalty
-  uint32_t *ram;           // this env's RAM block, one word per byte
+  const uint8_t *dec_op;   // general decoder: opcode -> operation | penalty << 7, then mode | cycles << 4
+  uint8_t *ram;            // this env's RAM block (shared memory, 4-byte aligned)
   IoCtx io;
   uint32_t A, X, Y, SP, PC, fc, fv, fn, fz, fdi;  // fdi holds the D (0x08) and I (0x04) bits
   uint32_t bank, jam, scheme;
@@ -463,7 +486,7 @@ struct FastConsoleT {
     const uint32_t w0 = w[0], w1 = w[1];
     A = w0 & 0xFF; X = (w0 >> 8) & 0xFF; Y = (w0 >> 16) & 0xFF; SP = w0 >> 24;
     setP(w1 & 0xFF); PC = w1 >> 16;
-    bank = (w1 >> 8) & (scheme == 2 ? 3u : scheme == 1 ? 1u : 0u);  // scheme is set before load
+    bank = (w1 >> 8) & (scheme == 3 ? 7u : scheme == 2 ? 3u : scheme == 1 ? 1u : 0u);  // scheme is set before load
     const uint64_t k = (uint64_t)w[2] | (uint64_t)w[3] << 32;
     io.Sset(IO_TCWLO, w[4]); io.Sset(IO_TCWHI, w[5]);
     const uint32_t w6 = w[6], w7 = w[7];
@@ -489,12 +512,11 @@ struct FastConsoleT {
     io.Sset(IO_LOGLO, 0); io.Sset(IO_LOGHI, 0); io.Sset(IO_LOGN, 0); io.Sset(IO_LOGCAP, 0);
     io.Sset(IO_STATUS, 0);
     const uint4 *r4 = reinterpret_cast<const uint4 *>(s + S::RAM);
+    uint32_t *r32 = reinterpret_cast<uint32_t *>(ram);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const uint4 v = r4[q];
-      const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int b = 0; b < 16; ++b) ram[q * 16 + b] = (ws[b >> 2] >> (8 * (b & 3))) & 0xFF;
+      r32[4 * q] = v.x; r32[4 * q + 1] = v.y; r32[4 * q + 2] = v.z; r32[4 * q + 3] = v.w;
     }
     status = 0; instret = 0; rounds = 0; pend = 0; vs_kf = ~0u;
     if constexpr (SPLIT) {
@@ -529,18 +551,9 @@ struct FastConsoleT {
     w[20] = (uint32_t)L0; w[21] = (uint32_t)(L0 >> 32);
     w[22] = frame_no; w[23] = 0;
     uint4 *r4 = reinterpret_cast<uint4 *>(s + S::RAM);
+    const uint32_t *r32 = reinterpret_cast<const uint32_t *>(ram);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      uint32_t ws[4];
-#pragma unroll
-      for (int k2 = 0; k2 < 4; ++k2) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) v |= (ram[q * 16 + k2 * 4 + b] & 0xFF) << (8 * b);
-        ws[k2] = v;
-      }
-      r4[q] = make_uint4(ws[0], ws[1], ws[2], ws[3]);
-    }
+    for (int q = 0; q < 8; ++q) r4[q] = make_uint4(r32[4 * q], r32[4 * q + 1], r32[4 * q + 2], r32[4 * q + 3]);
   }
   __device__ void snapshot(uint8_t *o) const { fc_snapshot(io, o, 0); }
   __device__ void set_log(uint32_t *p, uint32_t cap, uint8_t *bands) { fc_set_log(io, p, cap, bands); }
@@ -584,6 +597,7 @@ struct FastConsoleT {
   __device__ __forceinline__ void hotspot(uint32_t off) {
     if (scheme == 1) { if (off == 0xFF8 || off == 0xFF9) bank = off - 0xFF8; }
     else if (scheme == 2) { if (off >= 0xFF6 && off <= 0xFF9) bank = off - 0xFF6; }
+    else if (scheme == 3) { if (off >= 0xFF4 && off <= 0xFFB) bank = off - 0xFF4; }
   }
   __device__ __forceinline__ void note_vsync(uint32_t t) {
     if (vs_kf == ~0u) vs_kf = t;
@@ -770,7 +784,8 @@ struct FastConsoleT {
     const uint32_t k0 = kf;
     const uint32_t pc = PC;
     const uint32_t off = pc & 0xFFF;
-    if (!(pc & 0x1000) || off > (scheme ? 0xFF3u : 0xFFCu)) return false;
+    // no hot fetch may touch a hotspot: F8/F6 hotspots start at $FF6, F4's at $FF4
+    if (!(pc & 0x1000) || off > (scheme == 3 ? 0xFF1u : scheme ? 0xFF3u : 0xFFCu)) return false;
     const uint32_t b1 = (w >> 8) & 0xFF;
     const uint32_t a16 = (w >> 8) & 0xFFFF;
     uint32_t n;
@@ -782,6 +797,7 @@ struct FastConsoleT {
 #define ABY_ ((a16 + Y) & 0xFFFF)
 #define XPG(base, ea) ((((base) ^ (ea)) >> 8) & 1u)
 #define NZ(v) (fn = fz = (v))
+#define COLD_ if constexpr (COMPACT) return false;
 // read instructions: imm, zp, zp,X, abs, abs,X, abs,Y, (zp,X), (zp),Y
 #define RD_OPS(OPI, OPZ, OPZX, OPA, OPAX, OPAY, OPIX, OPIY, BODY)                                          \
   case OPI: { const uint32_t v = b1; BODY; n = 2; PC = pc + 2; break; }                                      \
@@ -792,10 +808,10 @@ struct FastConsoleT {
                PC = pc + 3; break; }                                                                          \
   case OPAY: { const uint32_t ea = ABY_; n = 4 + XPG(a16, ea); const uint32_t v = rd(ea, k0 + n - 1); BODY;   \
                PC = pc + 3; break; }                                                                          \
-  case OPIX: { const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;                          \
+  case OPIX: { COLD_ const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;                   \
                const uint32_t ea = ram[z & 0x7F] | ram[(z + 1) & 0x7F] << 8;                      \
                const uint32_t v = rd(ea, k0 + 5); BODY; n = 6; PC = pc + 2; break; }                           \
-  case OPIY: { if (!(b1 & 0x80) || b1 == 0xFF) return false;                                                  \
+  case OPIY: { COLD_ if (!(b1 & 0x80) || b1 == 0xFF) return false;                                           \
                const uint32_t base = ram[b1 & 0x7F] | ram[(b1 + 1) & 0x7F] << 8;                  \
                const uint32_t ea = (base + Y) & 0xFFFF; n = 5 + XPG(base, ea);                                \
                const uint32_t v = rd(ea, k0 + n - 1); BODY; PC = pc + 2; break; }
@@ -805,11 +821,11 @@ struct FastConsoleT {
 #define RMW_MEM_OPS(OPZ, OPZX, OPA, OPAX, FN)                                                                \
   case OPZ: { if (!(b1 & 0x80)) return false;                                                                 \
               ram[b1 & 0x7F] = FN(ram[b1 & 0x7F]); n = 5; PC = pc + 2; break; }                              \
-  case OPZX: { const uint32_t z = ZPX_; if (!(z & 0x80)) return false;                                        \
+  case OPZX: { COLD_ const uint32_t z = ZPX_; if (!(z & 0x80)) return false;                                 \
                ram[z & 0x7F] = FN(ram[z & 0x7F]); n = 6; PC = pc + 2; break; }                                \
-  case OPA: { if ((a16 & 0x1280) != 0x0080) return false;                                                     \
+  case OPA: { COLD_ if ((a16 & 0x1280) != 0x0080) return false;                                              \
               ram[a16 & 0x7F] = FN(ram[a16 & 0x7F]); n = 6; PC = pc + 3; break; }                            \
-  case OPAX: { const uint32_t ea = ABX_; if ((ea & 0x1280) != 0x0080) return false;                          \
+  case OPAX: { COLD_ const uint32_t ea = ABX_; if ((ea & 0x1280) != 0x0080) return false;                   \
                ram[ea & 0x7F] = FN(ram[ea & 0x7F]); n = 7; PC = pc + 3; break; }
 #define RMW_OPS(OPACC, OPZ, OPZX, OPA, OPAX, FN)                                                             \
   case OPACC: { A = FN(A); n = 2; PC = pc + 1; break; }                                                       \
@@ -852,17 +868,17 @@ struct FastConsoleT {
       case 0xC4: cmp(Y, rdz(b1, k0 + 2)); n = 3; PC = pc + 2; break;
       case 0xCC: cmp(Y, rd(a16, k0 + 3)); n = 4; PC = pc + 3; break;
       // BIT: zp, abs
-      case 0x24: { const uint32_t v = rdz(b1, k0 + 2); fn = v; fv = v & 0x40; fz = A & v; n = 3; PC = pc + 2; break; }
-      case 0x2C: { const uint32_t v = rd(a16, k0 + 3); fn = v; fv = v & 0x40; fz = A & v; n = 4; PC = pc + 3; break; }
+      case 0x24: { COLD_ const uint32_t v = rdz(b1, k0 + 2); fn = v; fv = v & 0x40; fz = A & v; n = 3; PC = pc + 2; break; }
+      case 0x2C: { COLD_ const uint32_t v = rd(a16, k0 + 3); fn = v; fv = v & 0x40; fz = A & v; n = 4; PC = pc + 3; break; }
       // stores
       case 0x85: sa = b1; sv = A; stc = k0 + 2; n = 3; PC = pc + 2; break;
       case 0x95: sa = ZPX_; sv = A; stc = k0 + 3; n = 4; PC = pc + 2; break;
       case 0x8D: sa = a16; sv = A; stc = k0 + 3; n = 4; PC = pc + 3; break;
       case 0x9D: sa = ABX_; sv = A; stc = k0 + 4; n = 5; PC = pc + 3; break;
       case 0x99: sa = ABY_; sv = A; stc = k0 + 4; n = 5; PC = pc + 3; break;
-      case 0x81: { const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;
+      case 0x81: { COLD_ const uint32_t z = ZPX_; if (!(z & 0x80) || z == 0xFF) return false;
                    sa = ram[z & 0x7F] | ram[(z + 1) & 0x7F] << 8; sv = A; stc = k0 + 5; n = 6; PC = pc + 2; break; }
-      case 0x91: { if (!(b1 & 0x80) || b1 == 0xFF) return false;
+      case 0x91: { COLD_ if (!(b1 & 0x80) || b1 == 0xFF) return false;
                    const uint32_t base = ram[b1 & 0x7F] | ram[(b1 + 1) & 0x7F] << 8;
                    sa = (base + Y) & 0xFFFF; sv = A; stc = k0 + 5; n = 6; PC = pc + 2; break; }
       case 0x86: sa = b1; sv = X; stc = k0 + 2; n = 3; PC = pc + 2; break;
@@ -903,11 +919,11 @@ struct FastConsoleT {
       IMPL(0xD8, { fdi &= ~0x08u; })
       IMPL(0xF8, { fdi |= 0x08u; })
       IMPL(0xEA, {})
-      case 0x48: if (!(SP & 0x80)) return false; ram[SP & 0x7F] = A; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
-      case 0x08: if (!(SP & 0x80)) return false; ram[SP & 0x7F] = P() | 0x10u; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
-      case 0x68: { const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
+      case 0x48: COLD_ if (!(SP & 0x80)) return false; ram[SP & 0x7F] = A; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
+      case 0x08: COLD_ if (!(SP & 0x80)) return false; ram[SP & 0x7F] = P() | 0x10u; SP = (SP - 1) & 0xFF; n = 3; PC = pc + 1; break;
+      case 0x68: { COLD_ const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
                    SP = s1; A = ram[s1 & 0x7F]; NZ(A); n = 4; PC = pc + 1; break; }
-      case 0x28: { const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
+      case 0x28: { COLD_ const uint32_t s1 = (SP + 1) & 0xFF; if (!(s1 & 0x80)) return false;
                    SP = s1; setP(ram[s1 & 0x7F]); n = 4; PC = pc + 1; break; }
       case 0x4C: PC = a16; n = 3; break;
       case 0x20: { if (SP < 0x81) return false;
@@ -925,6 +941,7 @@ struct FastConsoleT {
 #undef ABY_
 #undef XPG
 #undef NZ
+#undef COLD_
 #undef RD_OPS
 #undef RMW_MEM_OPS
 #undef RMW_OPS
@@ -946,10 +963,11 @@ struct FastConsoleT {
     pend = 0;
     const uint32_t pc = PC;
     const uint32_t opcode = rd(pc, k0);
-    const uint32_t op = dec_op[opcode];
+    const uint32_t opb = dec_op[opcode];
+    const uint32_t op = opb & 0x7F;
     const uint32_t info = dec_op[256 + opcode];
     const uint32_t mode = info & 0xF;
-    uint32_t n = (info >> 4) & 7;
+    uint32_t n = info >> 4;
     if (op == O_JAM) { jam = 1; status |= ST_ILLEGAL; return; }
     uint32_t b1 = 0, b2 = 0, ea = 0, cross = 0;
     if (mode >= IMM) b1 = rd(pc + 1, k0);
@@ -972,7 +990,7 @@ struct FastConsoleT {
                   ea = (b + Y) & 0xFFFF; cross = (b ^ ea) >> 8; PC = (pc + 2) & 0xFFFF; break; }
       default: PC = (pc + 2) & 0xFFFF; ea = (PC + (uint32_t)(int32_t)(int8_t)(uint8_t)b1) & 0xFFFF; break;
     }
-    if (cross && (info >> 7)) n++;
+    if (cross && (opb >> 7)) n++;
     instret++;
     if (mode == REL) {
       uint32_t take;
@@ -1022,6 +1040,36 @@ struct FastConsoleT {
         else { wr(ea, old, kA - 1); wr(ea, r, kA); }
         break;
       }
+      case O_SLO: case O_RLA: case O_SRE: case O_RRA: case O_DCP: case O_ISC: {
+        // read-modify-write of memory (both writes), then the accumulator operation
+        const uint32_t old = rd(ea, kA - 2);
+        uint32_t r, c = fc;
+        switch (op) {
+          case O_SLO: r = (old << 1) & 0xFF; c = old >> 7; break;
+          case O_RLA: r = ((old << 1) | fc) & 0xFF; c = old >> 7; break;
+          case O_SRE: r = old >> 1; c = old & 1; break;
+          case O_RRA: r = (old >> 1) | (fc << 7); c = old & 1; break;
+          case O_DCP: r = (old - 1) & 0xFF; break;
+          default: r = (old + 1) & 0xFF; break;
+        }
+        wr(ea, old, kA - 1);
+        wr(ea, r, kA);
+        switch (op) {
+          case O_SLO: A |= r; fc = c; fn = fz = A; break;
+          case O_RLA: A &= r; fc = c; fn = fz = A; break;
+          case O_SRE: A ^= r; fc = c; fn = fz = A; break;
+          case O_RRA: fc = c; adc(r); break;
+          case O_DCP: cmp(A, r); break;
+          default: sbc(r); break;
+        }
+        break;
+      }
+      case O_SAX: wr(ea, A & X, kA); break;
+      case O_LAX: A = rd(ea, kA); X = A; fn = fz = A; break;
+      case O_ANC: A &= b1; fn = fz = A; fc = A >> 7; break;
+      case O_ALR: A &= b1; fc = A & 1u; A >>= 1; fn = fz = A; break;
+      case O_SBX: { const uint32_t ax = A & X; fc = ax >= b1 ? 1u : 0u; X = (ax - b1) & 0xFF; fn = fz = X; break; }
+      case O_NOP: if (mode != IMP && mode != IMM) (void)rd(ea, kA); break;  // the operand read
       case O_INX: X = (X + 1) & 0xFF; fn = fz = X; break;
       case O_INY: Y = (Y + 1) & 0xFF; fn = fz = Y; break;
       case O_DEX: X = (X - 1) & 0xFF; fn = fz = X; break;
@@ -1074,7 +1122,7 @@ struct FastConsoleT {
         PC = lo | hi << 8;
         break;
       }
-      default: break;  // NOP
+      default: break;
     }
     uint32_t k = k0 + n;
     if (pend & IO_WSYNC) k = ((k + 75u) / 76u) * 76u;
@@ -1108,7 +1156,7 @@ struct FastConsoleT {
       if (lead == 0xFFFFFFFFu) break;
       ++rounds;
       if (active && PC == (lead & 0xFFFFu)) {
-        if (!exec(w)) fc_exec_general<SPLIT>(this);
+        if (!exec(w)) fc_exec_general<SPLIT, COMPACT>(this);
         if (jam | (vs_kf != ~0u) | (kf >= 76u * CAP_LINES)) {
           if (jam) next_rel = kf / 76u;
           else if (vs_kf != ~0u) next_rel = vs_kf / 76u;
@@ -1124,17 +1172,17 @@ struct FastConsoleT {
   }
 };
 
-using FastConsole = FastConsoleT<false>;
+using FastConsole = FastConsoleT<false, false>;
 
 // Out-of-line general instruction on a copy of the console.  Only the CPU
 // and timing state comes back: the caller's pointers into shared memory are
 // never reloaded from the copy, so they keep their shared address space.
-template <bool SPLIT>
-__device__ __noinline__ void fc_exec_general_impl(FastConsoleT<SPLIT> *c) { c->exec_general(); }
-template <bool SPLIT>
-__device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT> *self) {
-  FastConsoleT<SPLIT> tmp = *self;
-  fc_exec_general_impl<SPLIT>(&tmp);
+template <bool SPLIT, bool COMPACT>
+__device__ __noinline__ void fc_exec_general_impl(FastConsoleT<SPLIT, COMPACT> *c) { c->exec_general(); }
+template <bool SPLIT, bool COMPACT>
+__device__ __forceinline__ void fc_exec_general(FastConsoleT<SPLIT, COMPACT> *self) {
+  FastConsoleT<SPLIT, COMPACT> tmp = *self;
+  fc_exec_general_impl<SPLIT, COMPACT>(&tmp);
   self->A = tmp.A; self->X = tmp.X; self->Y = tmp.Y; self->SP = tmp.SP; self->PC = tmp.PC;
   self->fc = tmp.fc; self->fv = tmp.fv; self->fn = tmp.fn; self->fz = tmp.fz; self->fdi = tmp.fdi;
   self->bank = tmp.bank; self->jam = tmp.jam; self->kf = tmp.kf; self->pend = tmp.pend; self->vs_kf = tmp.vs_kf;

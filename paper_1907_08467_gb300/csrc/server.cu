@@ -75,6 +75,7 @@ size_t tick_device_bytes(int tick_envs, int n_roms) {
 struct TickCtx {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t t_begin = nullptr, t_end = nullptr;  // timing events around the tick's device work
   uint8_t *h_in = nullptr, *h_out = nullptr;   // pinned
   uint8_t *d_in = nullptr, *d_obs = nullptr, *d_out = nullptr;
   int *d_queue = nullptr;
@@ -98,6 +99,10 @@ struct atari_server {
   std::string fatal_msg;
   uint64_t ticks = 0, requests = 0, env_steps = 0, launches = 0;
   uint64_t tick_env_sum = 0;
+  // device overlap of ticks: times (ms after t_ref) of the tick ends seen so far
+  cudaEvent_t t_ref = nullptr;
+  double last_end_ms = -1.0;
+  uint64_t overlapped_ticks = 0;
 };
 
 namespace {
@@ -120,6 +125,7 @@ int launch_tick(atari_server *S, TickCtx &c) {
   std::memcpy(c.h_in + L.init_off, p.init.data(), p.init.size() * 4);
   std::memcpy(c.h_in + L.act_off, p.actions.data(), p.actions.size());
   const size_t in_bytes = L.act_off + (size_t)p.n_active;
+  SRV_CUDA(cudaEventRecord(c.t_begin, c.stream), ATARI_ECUDA);
   SRV_CUDA(cudaMemcpyAsync(c.d_in, c.h_in, in_bytes, cudaMemcpyHostToDevice, c.stream), ATARI_ECUDA);
   atari_internal::ServeTick t;
   t.d_blob = reinterpret_cast<const int32_t *>(c.d_in + L.blob_off);
@@ -148,6 +154,7 @@ int launch_tick(atari_server *S, TickCtx &c) {
       c.pageable.push_back(r);
     }
   }
+  SRV_CUDA(cudaEventRecord(c.t_end, c.stream), ATARI_ECUDA);
   SRV_CUDA(cudaEventRecord(c.done, c.stream), ATARI_ECUDA);
   return 0;
 }
@@ -200,6 +207,10 @@ void completer_main(atari_server *S) {
       msg = std::string("serving tick: ") + cudaGetErrorString(e);
     }
     const TickPlan &p = c.plan;
+    // where the tick ran on the device, in ms after the server's reference event
+    float t_b = 0.0f, t_e = 0.0f;
+    const bool timed = !status && cudaEventElapsedTime(&t_b, S->t_ref, c.t_begin) == cudaSuccess &&
+                       cudaEventElapsedTime(&t_e, S->t_ref, c.t_end) == cudaSuccess;
     if (!status) {
       const int32_t *rew = reinterpret_cast<const int32_t *>(c.h_out);
       const uint8_t *done = c.h_out + 4 * (size_t)p.n_active;
@@ -228,6 +239,12 @@ void completer_main(atari_server *S) {
       r->finished = true;
     }
     S->sched->finish_tick(p, t);
+    if (timed) {
+      // ticks complete in launch order: this one overlapped an earlier one on
+      // the device when it began before the latest earlier end
+      if (S->last_end_ms >= 0.0 && (double)t_b < S->last_end_ms) S->overlapped_ticks++;
+      S->last_end_ms = std::max(S->last_end_ms, (double)t_e);
+    }
     S->ticks++;
     S->launches += 2 + (p.n_init > 0 ? 1 : 0);
     S->requests += p.reqs.size();
@@ -243,6 +260,8 @@ void free_server(atari_server *S) {
   for (TickCtx &c : S->ctx) {
     if (c.stream) cudaStreamSynchronize(c.stream);
     if (c.done) cudaEventDestroy(c.done);
+    if (c.t_begin) cudaEventDestroy(c.t_begin);
+    if (c.t_end) cudaEventDestroy(c.t_end);
     if (c.stream) cudaStreamDestroy(c.stream);
     if (c.h_in) cudaFreeHost(c.h_in);
     if (c.h_out) cudaFreeHost(c.h_out);
@@ -251,6 +270,7 @@ void free_server(atari_server *S) {
     if (c.d_out) cudaFree(c.d_out);
     if (c.d_queue) cudaFree(c.d_queue);
   }
+  if (S->t_ref) cudaEventDestroy(S->t_ref);
   if (S->env) atari_env_destroy(S->env);
   delete S;
 }
@@ -352,6 +372,8 @@ int atari_server_create(const uint8_t *const *roms, const size_t *rom_sizes, con
     TickCtx &c = S->ctx[(size_t)i];
     cudaError_t e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming | cudaEventBlockingSync);
+    if (e == cudaSuccess) e = cudaEventCreate(&c.t_begin);
+    if (e == cudaSuccess) e = cudaEventCreate(&c.t_end);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&c.h_in, L.bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&c.h_out, align_up(5 * (size_t)tick_cap, 256), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_in, L.bytes);
@@ -364,6 +386,15 @@ int atari_server_create(const uint8_t *const *roms, const size_t *rom_sizes, con
       return set_error(code, std::string("server tick buffers: ") + cudaGetErrorString(e));
     }
     S->free_ctx.push_back(i);
+  }
+  {
+    cudaError_t e = cudaEventCreate(&S->t_ref);
+    if (e == cudaSuccess) e = cudaEventRecord(S->t_ref, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(S->t_ref);
+    if (e != cudaSuccess) {
+      free_server(S);
+      return set_error(ATARI_ECUDA, std::string("server timing event: ") + cudaGetErrorString(e));
+    }
   }
   S->launcher = std::thread(launcher_main, S);
   S->completer = std::thread(completer_main, S);
@@ -449,6 +480,7 @@ int atari_server_get_stats(atari_server *S, atari_server_stats *out) {
   out->free_slots = S->sched->free_slots();
   out->queued_sessions = S->sched->queued_sessions();
   out->pending_requests = S->sched->pending_requests();
+  out->overlapped_ticks = S->overlapped_ticks;
   return 0;
 }
 

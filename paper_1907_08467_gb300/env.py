@@ -28,7 +28,7 @@ class _Config(C.Structure):
                 ("startup_frames", C.c_int), ("max_noops", C.c_int), ("output_mode", C.c_int),
                 ("form", C.c_int), ("log_cap", C.c_int), ("envs_per_block", C.c_int),
                 ("envs_per_warp", C.c_int), ("raster_warps_per_frame", C.c_int), ("seed", C.c_uint64),
-                ("tia_warps", C.c_int), ("grouping", C.c_int)]
+                ("tia_warps", C.c_int), ("grouping", C.c_int), ("dispatch", C.c_int)]
 
 
 class _Meta(C.Structure):
@@ -111,9 +111,10 @@ def _check(rc: int):
 
 def make_config(frameskip=4, sticky=False, n_cache=30, startup_frames=64, max_noops=30,
                 output_mode=OUT_STACK, form=FORM_PLAIN, log_cap=4096, envs_per_block=0, envs_per_warp=0,
-                raster_warps_per_frame=0, seed=1, tia_warps=0, grouping=0) -> _Config:
+                raster_warps_per_frame=0, seed=1, tia_warps=0, grouping=0, dispatch=0) -> _Config:
     return _Config(frameskip, int(sticky), n_cache, startup_frames, max_noops, output_mode, form,
-                   log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed, tia_warps, grouping)
+                   log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed, tia_warps, grouping,
+                   dispatch)
 
 
 def footprint(n_envs: int, n_roms: int, **cfg) -> int:
@@ -296,7 +297,8 @@ class AtariEnv:
 
     def launch_shape(self):
         """(envs per warp, envs per block, warps per frame, interpreter grid,
-        tia_warps: 2 with paired TIA warps, else 1, grouping: 1 env order, 2 bank-aware)."""
+        tia_warps: 2 with paired TIA warps, else 1, grouping: 1 env order, 2 bank-aware, + 4 with the
+        compact opcode switch)."""
         v = [C.c_int() for _ in range(6)]
         _check(self.lib.atari_env_launch_shape(self.h, *[C.byref(x) for x in v]))
         return tuple(x.value for x in v)

@@ -28,7 +28,8 @@ class _Stats(C.Structure):
     _fields_ = [("ticks", C.c_uint64), ("requests", C.c_uint64), ("env_steps", C.c_uint64),
                 ("sessions_admitted", C.c_uint64), ("launches", C.c_uint64), ("budget_bytes", C.c_uint64), ("bytes_in_use", C.c_uint64),
                 ("fixed_bytes", C.c_uint64), ("per_env_bytes", C.c_uint64), ("capacity", C.c_int),
-                ("free_slots", C.c_int), ("queued_sessions", C.c_int), ("pending_requests", C.c_int)]
+                ("free_slots", C.c_int), ("queued_sessions", C.c_int), ("pending_requests", C.c_int),
+                ("overlapped_ticks", C.c_uint64)]
 
 
 class _LoadgenConfig(C.Structure):

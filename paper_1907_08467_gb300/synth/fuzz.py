@@ -6,8 +6,10 @@ fills every line with a random block of legal instructions drawn from the
 whole documented instruction set: ALU and decimal arithmetic, every
 addressing mode, read-modify-write on RAM and on TIA strobe registers, TIA
 and RIOT reads and writes, balanced stack operations, short branches and a
-subroutine call.  Optionally one line holds an undocumented opcode, which
-halts the CPU.  Random stores stay in RAM $80-$EF and the frame counter and
+subroutine call.  Optionally the blocks also use the stable undocumented
+opcodes (read-modify-write plus accumulator operations on RAM and on TIA
+strobes, SAX, LAX, ANC, ALR, SBX, SBC $EB and the NOPs of one to three
+bytes), and optionally one line holds an opcode that halts the CPU.  Random stores stay in RAM $80-$EF and the frame counter and
 game-over byte live at $F1 / $F2, which only the skeleton writes.
 """
 from __future__ import annotations
@@ -27,7 +29,37 @@ RIOT_R = [0x280, 0x281, 0x282, 0x283, 0x284, 0x285, 0x28C, 0x2A4]
 RIOT_W = [0x281, 0x283, 0x294, 0x295, 0x296, 0x297, 0x280]
 
 
-def _block(rng: random.Random, budget: int, tag: str) -> str:
+def _undoc(rng: random.Random, emit, ram: int):
+    """One stable undocumented instruction (worst-case cycles counted)."""
+    r = rng.random()
+    if r < 0.30:
+        emit(f"{rng.choice(['SLO', 'RLA', 'SRE', 'RRA', 'DCP', 'ISC'])} ${ram:02X}", 5)
+    elif r < 0.40:
+        emit(f"{rng.choice(['SLO', 'DCP', 'ISC'])} ${rng.choice(TIA_STROBES):02X}", 5)
+    elif r < 0.48:
+        emit("TXA", 2); emit("AND #$6F", 2); emit("TAX", 2)
+        emit(f"{rng.choice(['SLO', 'RLA', 'SRE', 'RRA', 'DCP', 'ISC'])} $80,X", 6)
+    elif r < 0.56:
+        emit(f"SAX ${rng.choice([ram, rng.choice(TIA_W)]):02X}", 3)
+    elif r < 0.66:
+        emit(f"LAX ${rng.choice([ram, rng.randrange(16)]):02X}", 3)
+    elif r < 0.72:
+        emit(f"LAX (${0xE0 + 2 * rng.randrange(4):02X}),Y", 6)
+    elif r < 0.84:
+        emit(f"{rng.choice(['ANC', 'ALR', 'SBX'])} #${rng.randrange(256):02X}", 2)
+    elif r < 0.88:
+        emit(f".byte $EB, ${rng.randrange(256):02X}", 2)
+    elif r < 0.92:
+        emit(f".byte ${rng.choice([0x1A, 0x3A, 0x5A, 0x7A, 0xDA, 0xFA]):02X}", 2)
+    elif r < 0.95:
+        emit(f".byte ${rng.choice([0x80, 0x82, 0x89, 0xC2, 0xE2]):02X}, ${rng.randrange(256):02X}", 2)
+    elif r < 0.98:
+        emit(f".byte ${rng.choice([0x04, 0x44, 0x64, 0x14, 0x34]):02X}, ${ram:02X}", 4)
+    else:
+        emit(f".byte $0C, ${ram:02X}, $00", 4)
+
+
+def _block(rng: random.Random, budget: int, tag: str, undoc: bool = False) -> str:
     """Random straight-line code of at most `budget` cycles (worst case)."""
     out, used, k = [], 0, 0
 
@@ -38,6 +70,9 @@ def _block(rng: random.Random, budget: int, tag: str) -> str:
 
     while used < budget - 8:
         k += 1
+        if undoc and rng.random() < 0.25:
+            _undoc(rng, emit, 0x80 + rng.randrange(0x70))
+            continue
         r = rng.random()
         ram = 0x80 + rng.randrange(0x70)          # leave $F0-$FF to the stack
         if r < 0.16:
@@ -94,9 +129,10 @@ def _block(rng: random.Random, budget: int, tag: str) -> str:
     return "\n".join("        " + s if not s.endswith(":") else s for s in out) + "\n"
 
 
-def fuzz_rom(seed: int, jam: bool = False, lines: int = 24) -> Rom:
+def fuzz_rom(seed: int, jam: bool = False, lines: int = 24, undoc: bool = False) -> Rom:
     """A cartridge whose frames are made of random blocks (see module doc).
-    `lines` visible lines get random blocks (the rest of the 192 are plain)."""
+    `lines` visible lines get random blocks (the rest of the 192 are plain);
+    `undoc` mixes the stable undocumented opcodes into every block."""
     rng = random.Random(0xF000 + seed)
     src = """
         .org $F000
@@ -121,7 +157,7 @@ Main:   LDA #2
         CLD
 """
     for v in range(4):
-        src += _block(rng, 60, f"v{v}") + "        STA WSYNC\n"
+        src += _block(rng, 60, f"v{v}", undoc) + "        STA WSYNC\n"
     src += """
         LDX #32
 VbW:    STA WSYNC
@@ -136,7 +172,7 @@ VbW:    STA WSYNC
     for ln in range(lines):
         if ln == jam_line:
             src += f"        LDA $F1\n        CMP #{jam_at}\n        BNE NoJam\n        .byte $02\nNoJam:\n"
-        src += _block(rng, 62, f"l{ln}") + "        STA WSYNC\n"
+        src += _block(rng, 62, f"l{ln}", undoc) + "        STA WSYNC\n"
     src += f"""
         LDX #{192 - lines}
 VisW:   STA WSYNC
@@ -146,7 +182,7 @@ VisW:   STA WSYNC
         STA VBLANK
 """
     for o in range(3):
-        src += _block(rng, 60, f"o{o}") + "        STA WSYNC\n"
+        src += _block(rng, 60, f"o{o}", undoc) + "        STA WSYNC\n"
     src += """
         INC $F1
         LDA $F1
@@ -173,4 +209,5 @@ Table:  .byte %s
         .word Reset, Reset, Reset
 """ % (rng.randrange(130, 250), ", ".join(f"${rng.randrange(256):02X}" for _ in range(64)))
     data = Assembler().assemble(src, org=0xF000, size=4096)
-    return Rom(f"fuzz-{seed}{'-jam' if jam else ''}", data, 0x83, 0xF2, {"family": "fuzz"})
+    return Rom(f"fuzz-{seed}{'-jam' if jam else ''}{'-undoc' if undoc else ''}", data, 0x83, 0xF2,
+               {"family": "fuzz"})

@@ -523,17 +523,20 @@ LfDone:
 
 
 def rom_banked(seed: int, scheme: str) -> Rom:
-    """Batching family: 4 KB, F8 (8 KB) or F6 (16 KB) with code in every bank.
+    """Batching family: 4 KB, F8 (8 KB), F6 (16 KB) or F4 (32 KB) with code in
+    every bank.
 
     Bank 0 holds reset and the frame loop with RIOT-timer VBLANK and overscan
     waits.  The game logic runs in the last bank and the visible kernel in
     bank 1 (4 KB carts keep everything in one bank).  Banks are entered
     through stubs at $FFC0 + 6 j, identical in every bank: touch hotspot j,
-    then JMP to bank j's entry ($F000 for j >= 1, $F800 for bank 0).
+    then JMP to bank j's entry ($F000 for j >= 1, $F800 for bank 0).  F4's
+    hotspots start at $FFF4, so its stubs sit lower, at $FF80 + 6 j.
     """
     rng = random.Random(0x3000 + seed)
-    nbanks = {"4k": 1, "f8": 2, "f6": 4}[scheme]
-    hot0 = {"4k": None, "f8": 0x1FF8, "f6": 0x1FF6}[scheme]
+    nbanks = {"4k": 1, "f8": 2, "f6": 4, "f4": 8}[scheme]
+    hot0 = {"4k": None, "f8": 0x1FF8, "f6": 0x1FF6, "f4": 0x1FF4}[scheme]
+    stub_base = 0xFF80 if scheme == "f4" else 0xFFC0
     score, gameover = SCORE_SLOTS[seed % 3]
     sprites = rng.random() < 0.5
     init, pat = _init_block(rng, sprites=sprites)
@@ -584,7 +587,7 @@ VbWait: LDA INTIM
     tables = _tables(rng, pat, sprites)
 
     def stubs():
-        s = "        .org $FFC0\n"
+        s = f"        .org ${stub_base:04X}\n"
         for j in range(nbanks):
             s += f"Stub{j}: BIT ${hot0 + j:04X}\n        JMP ${0xF800 if j == 0 else 0xF000:04X}\n"
         s += f"ResetStub: BIT ${hot0:04X}\n        JMP Reset\n"

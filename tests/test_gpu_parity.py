@@ -76,6 +76,11 @@ FORMS = {
                                  tia_warps=2, grouping=2),
     "batched-8x16-w1-bank": dict(form=FORM_BATCHED, envs_per_warp=8, envs_per_block=16, raster_warps_per_frame=1,
                                  grouping=2),
+    # the compact hot opcode switch (rare forms through the general decoder)
+    "split-32x64-w4-compact": dict(form=FORM_BATCHED, envs_per_warp=32, envs_per_block=64, raster_warps_per_frame=4,
+                                   tia_warps=2, dispatch=2),
+    "batched-16x32-w2-compact": dict(form=FORM_BATCHED, envs_per_warp=16, envs_per_block=32,
+                                     raster_warps_per_frame=2, tia_warps=1, dispatch=2),
 }
 
 
@@ -130,24 +135,42 @@ def test_sprite_family_stack_output(form):
 
 
 @pytest.mark.parametrize("form", ["plain", "batched-auto", "batched-8x16-w1", "split-8x16-w2", "split-32x128-w4-bank",
-                                  "batched-8x16-w1-bank"])
+                                  "batched-8x16-w1-bank", "split-32x64-w4-compact"])
 def test_banked_sticky_family(form):
     """32 cartridges mixing 4 KB, F8 and F6 with code in every bank, RIOT-timer
     frame timing and sticky actions drawn from the per-env Philox stream."""
     w = synth.workload(3, n_envs=64)
     g, o = pair(w.roms, w.env_rom, output_mode=OUT_STACK, sticky=True, seed=w.seed, **FORMS[form])
     if form.endswith("bank"):
-        assert g.launch_shape()[5] == 2      # the env list is regrouped by bank every step
+        assert g.launch_shape()[5] & 3 == 2      # the env list is regrouped by bank every step
+    if form.endswith("compact"):
+        assert g.launch_shape()[5] & 4           # the compact opcode switch runs
     acts = synth.actions(13, 80, 64)
     run_parity(g, o, acts, check_frames=True)
 
 
-@pytest.mark.parametrize("seed0,form", [(0, "plain"), (8, "plain"), (0, "batched-auto"), (16, "batched-8x16-w1"),
-                                        (24, "split-32x128-w4")])
-def test_fuzz_programs(seed0, form):
+@pytest.mark.parametrize("form", ["plain", "batched-auto", "split-8x16-w2", "split-32x128-w4-bank"])
+def test_f4_cartridges(form):
+    """32 KB F4 cartridges (eight banks, hotspots $1FF4-$1FFB) with code in
+    three banks and sticky actions, mixed with a 4 KB and an F6 cartridge
+    (the batched form stages 32 KB per block)."""
+    roms = [synth.rom_banked(s, "f4") for s in (1, 2, 3)] + [synth.rom_banked(4, "4k"), synth.rom_banked(5, "f6")]
+    env_rom = [i % 5 for i in range(40)]
+    g, o = pair(roms, env_rom, output_mode=OUT_STACK, sticky=True, seed=6, **FORMS[form])
+    run_parity(g, o, synth.actions(71, 50, 40), check_frames=True)
+
+
+@pytest.mark.parametrize("seed0,form,undoc", [(0, "plain", False), (8, "plain", False), (0, "batched-auto", False),
+                                              (16, "batched-8x16-w1", False), (24, "split-32x128-w4", False),
+                                              (32, "plain", True), (40, "batched-auto", True),
+                                              (48, "split-8x16-w2", True), (56, "batched-8x16-w1", True),
+                                              (64, "split-32x64-w4-compact", False),
+                                              (72, "batched-16x32-w2-compact", True)])
+def test_fuzz_programs(seed0, form, undoc):
     """Random-program cartridges (all documented opcodes, decimal mode, RMW on
-    TIA strobes, TIA/RIOT reads, halting opcodes) stepped on both sides."""
-    roms = [synth.fuzz_rom(seed0 + s, jam=s % 3 == 0) for s in range(8)]
+    TIA strobes, TIA/RIOT reads, halting opcodes; with `undoc` also the stable
+    undocumented opcodes, on RAM and on TIA strobes) stepped on both sides."""
+    roms = [synth.fuzz_rom(seed0 + s, jam=s % 3 == 0, undoc=undoc) for s in range(8)]
     env_rom = [i % 8 for i in range(64)]
     g, o = pair(roms, env_rom, output_mode=OUT_STACK, seed=5, **FORMS[form])
     acts = synth.actions(14 + seed0, 60, 64)

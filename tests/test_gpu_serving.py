@@ -176,3 +176,21 @@ def test_loadgen_smoke(roms):
     st = srv.stats()
     assert st["free_slots"] == st["capacity"] and st["pending_requests"] == 0
     srv.close()
+
+
+@pytest.mark.parametrize("inflight", [1, 2])
+def test_ticks_overlap_on_the_device(roms, inflight):
+    """Continuous batching overlaps ticks on the GPU, not only on the host:
+    with two tick contexts in flight and enough clients to keep both busy,
+    ticks begin on the device (CUDA events on their streams) before the
+    previous tick has ended; with one context they never do."""
+    srv = _server(roms, budget_bytes=4 << 30, max_slots=4096, inflight=inflight)
+    r = srv.loadgen(n_clients=32, seconds=3.0, think_mean_ms=0.5, min_envs=64, max_envs=256,
+                    session_steps_mean=20, seed=7, want_obs=True)
+    st = srv.stats()
+    srv.close()
+    assert r["ticks"] >= 10
+    if inflight == 1:
+        assert st["overlapped_ticks"] == 0
+    else:
+        assert st["overlapped_ticks"] > 0, (st["overlapped_ticks"], r["ticks"])
