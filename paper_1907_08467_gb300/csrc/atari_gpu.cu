@@ -134,6 +134,18 @@ std::vector<uint32_t> build_decode_table() {
   return t;
 }
 
+// The batched console's decode bytes: per opcode, operation | page-cross
+// penalty << 7, then mode | cycles << 4.
+std::vector<uint8_t> build_dec_op(const std::vector<uint32_t> &dec) {
+  std::vector<uint8_t> d(512, 0);
+  for (int o = 0; o < 256; ++o) {
+    const uint32_t t = dec[o];
+    d[o] = (uint8_t)((t & 0x7F) | ((t >> 16) & 1u) << 7);
+    d[256 + o] = (uint8_t)(((t >> 8) & 0xFu) | ((t >> 12) & 0xFu) << 4);
+  }
+  return d;
+}
+
 int scheme_of(size_t sz);
 
 // Cartridge info word: scheme | score RAM index << 8 | game-over RAM index
@@ -174,33 +186,50 @@ __device__ void reset_from_cache(uint8_t *st, const uint8_t *cache, const uint32
   Console<GlobalMem>::st32(st + S::EPISODE, episode);
 }
 
-// One thread per ROM: from power-on, run the start-up frames, then keep a
-// snapshot after each of the next max_noops + 1 frames.
-__global__ void k_cache_run(uint8_t *work, uint8_t *snaps, const uint8_t *roms, const uint32_t *info,
-                            const uint32_t *dec_g, int n_roms, int startup, int max_noops) {
-  __shared__ uint32_t dec[256];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) dec[i] = dec_g[i];
+// One block per ROM: from power-on, run the start-up frames, then keep a
+// snapshot after each of the next max_noops + 1 frames.  Lane 0 runs the
+// batched form's console (RAM, I/O state and the staged cartridge in shared
+// memory), which steps the same machine as the plain console and is far
+// faster than it for one sequential trajectory; the block stages the
+// cartridge.  rom_stage = bytes of the largest cartridge.
+__global__ void __launch_bounds__(128) k_cache_run(uint8_t *work, uint8_t *snaps, const uint8_t *roms,
+                                                    const uint32_t *info, const uint8_t *dec_op_g, int rom_stage,
+                                                    int startup, int max_noops) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t *rom8 = smem;                                   // rom_stage bytes, then 16 of padding
+  uint8_t *dec_op = smem + (size_t)rom_stage + 16;
+  uint8_t *ram = dec_op + 512;
+  uint32_t *iow = reinterpret_cast<uint32_t *>(ram + RAM_BYTES);
+  uint8_t *tia = reinterpret_cast<uint8_t *>(iow + IO_STRIDE);
+  const int r = blockIdx.x;
+  const uint32_t inf = info[r];
+  const uint32_t banks = inf >> 24;
+  const uint4 *src = reinterpret_cast<const uint4 *>(roms + (size_t)r * ROM_SLOT);
+  uint4 *dst = reinterpret_cast<uint4 *>(rom8);
+  for (uint32_t q = threadIdx.x; q < banks * 256u; q += blockDim.x) dst[q] = src[q];
+  if (threadIdx.x == 0) dst[banks * 256u] = make_uint4(0, 0, 0, 0);
+  for (int t = threadIdx.x; t < 512; t += blockDim.x) dec_op[t] = dec_op_g[t];
   __syncthreads();
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n_roms) return;
+  if (threadIdx.x != 0) return;
   uint8_t *st = work + (size_t)r * 256;
-  Console<GlobalMem> m;
-  m.mem.ram = st + S::RAM;
-  m.mem.rom = roms + (size_t)r * ROM_SLOT;
-  m.dec = dec;
-  m.log.rec = nullptr;
-  m.log.n = 0;
-  m.log.cap = 0;
-  m.scheme = rom_info(info, r).scheme;
+  FastConsoleT<false, false> m;
+  m.rom8 = rom8;
+  m.dec_op = dec_op;
+  m.ram = ram;
+  m.io = IoCtx{tia, iow};
+  m.scheme = inf & 0xFF;
+  m.wmask = 1u;
   m.load(st);
+  m.set_log(nullptr, 0, nullptr);
   for (int f = 0; f < startup; ++f) {
     m.apply_action(0);
     m.run_frame();
   }
   for (int j = 0; j <= max_noops; ++j) {
     m.store(st);
-    uint8_t *dst = snaps + ((size_t)r * (max_noops + 1) + j) * 256;
-    for (int b = 0; b < 256; ++b) dst[b] = st[b];
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(st);
+    uint4 *d4 = reinterpret_cast<uint4 *>(snaps + ((size_t)r * (max_noops + 1) + j) * 256);
+    for (int q = 0; q < 16; ++q) d4[q] = s4[q];
     if (j < max_noops) {
       m.apply_action(0);
       m.run_frame();
@@ -731,13 +760,13 @@ size_t atari_env_footprint(int n_envs, int n_roms, const atari_config *cfg) {
   if (!cfg || n_envs < 0 || n_roms < 0) return 0;
   size_t n = (size_t)n_envs;
   size_t b = 0;
-  b += (size_t)n_roms * ROM_SLOT + (size_t)n_roms * 4 + 1024;
+  b += (size_t)n_roms * ROM_SLOT + (size_t)n_roms * 4 + 1024 + 512;  // images, info, decode word and byte tables
   b += n * (4 + 4 + 256);                                 // env_rom, env_key, state
   b += (size_t)n_roms * cfg->n_cache * 256;               // cache
   b += n * 2 * (size_t)cfg->log_cap * 4;                  // log
   b += n * 2 * 64 + n * 2 * 2 * 4;                        // snapshots, meta
   if (cfg->form == ATARI_FORM_PLAIN) b += n * 2 * 210 * 160;   // frames (plain form only)
-  else b += (size_t)n_roms * ROMB_SLOT + 512 + n * 8 + 64 + (size_t)(n_roms + 1) * 4;  // stage bytes, work items, regrouping
+  else b += (size_t)n_roms * ROMB_SLOT + n * 8 + 64 + (size_t)(n_roms + 1) * 4;  // stage bytes, work items, regrouping
   if (cfg->output_mode == ATARI_OUT_STACK) b += n * 4 * 7056 + n;
   if (cfg->output_mode == ATARI_OUT_STACK && cfg->form == ATARI_FORM_BATCHED) b += n * 2 * 3 * 64;  // band snapshots
   b += n * (4 + 1 + 12 + 1);                              // rewards, dones, counters, action staging
@@ -785,7 +814,7 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
       (rc = dalloc(&E->d_meta, n * 2 * 2 * 4, T)) ||
       (c.form == ATARI_FORM_PLAIN && (rc = dalloc(&E->d_frames, n * 2 * 210 * 160, T))) ||
       (rc = dalloc(&E->d_rew, n * 4, T)) || (rc = dalloc(&E->d_done, n, T)) || (rc = dalloc(&E->d_ctr, n * 12, T)) ||
-      (rc = dalloc(&E->d_act, n, T)) || (rc = dalloc(&E->d_luma, 128, T)))
+      (rc = dalloc(&E->d_act, n, T)) || (rc = dalloc(&E->d_luma, 128, T)) || (rc = dalloc(&E->d_dec_op, 512, T)))
     return bail(rc);
   if (c.output_mode == ATARI_OUT_STACK) {
     if ((rc = dalloc(&E->d_ring, n * 4 * 7056, T)) || (rc = dalloc(&E->d_head, n, T))) return bail(rc);
@@ -831,8 +860,9 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
     cudaError_t e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice);
     return e == cudaSuccess ? 0 : fail(ATARI_ECUDA, std::string("upload: ") + cudaGetErrorString(e));
   };
+  const std::vector<uint8_t> dec_op = build_dec_op(dec);
   if ((rc = up(E->d_roms, img.data(), img.size())) || (rc = up(E->d_info, info.data(), info.size() * 4)) ||
-      (rc = up(E->d_dec, dec.data(), 1024)) || (rc = up(E->d_env_rom, env_rom, n * 4)) ||
+      (rc = up(E->d_dec, dec.data(), 1024)) || (rc = up(E->d_dec_op, dec_op.data(), 512)) || (rc = up(E->d_env_rom, env_rom, n * 4)) ||
       (rc = up(E->d_env_key, keys.data(), n * 4)))
     return bail(rc);
   if (luma && (rc = up(E->d_luma, luma, 128))) return bail(rc);
@@ -847,7 +877,11 @@ int atari_env_create(const uint8_t *const *roms, const size_t *rom_sizes, const 
   }
   rc = up(d_work, power.data(), power.size());
   if (!rc) {
-    k_cache_run<<<(n_roms + 31) / 32, 32>>>(d_work, d_snaps, E->d_roms, E->d_info, E->d_dec, n_roms,
+    uint32_t max_banks = 1;
+    for (int r = 0; r < n_roms; ++r) max_banks = std::max(max_banks, E->h_banks[r]);
+    const int stage = (int)max_banks * 4096;
+    const size_t cache_smem = (size_t)stage + 16 + 512 + RAM_BYTES + 4 * IO_STRIDE + TIA_STRIDE;
+    k_cache_run<<<n_roms, 128, cache_smem>>>(d_work, d_snaps, E->d_roms, E->d_info, E->d_dec_op, stage,
                                            c.startup_frames, c.max_noops);
     int tot = n_roms * c.n_cache;
     k_cache_pick<<<(tot + 127) / 128, 128>>>(E->d_cache, d_snaps, n_roms, c.n_cache, c.max_noops, c.seed);
@@ -1152,13 +1186,7 @@ int autotune(atari_env *E) {
 int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vector<uint32_t> &dec) {
   const int R = E->n_roms;
   std::vector<uint8_t> bytes((size_t)R * ROMB_SLOT, 0u);
-  std::vector<uint8_t> dec_op(512, 0);
-  // per opcode: operation | page-cross penalty << 7, then mode | cycles << 4
-  for (int o = 0; o < 256; ++o) {
-    const uint32_t t = dec[o];
-    dec_op[o] = (uint8_t)((t & 0x7F) | ((t >> 16) & 1u) << 7);
-    dec_op[256 + o] = (uint8_t)(((t >> 8) & 0xFu) | ((t >> 12) & 0xFu) << 4);
-  }
+  (void)dec;  // the decode bytes were uploaded at create for the start-state cache
   uint32_t max_banks = 1;
   for (int r = 0; r < R; ++r) {
     const uint32_t banks = E->h_banks[r];
@@ -1171,10 +1199,8 @@ int setup_batched(atari_env *E, const std::vector<uint8_t> &img, const std::vect
   if (int rc = dalloc(&E->d_seg, (size_t)(R + 1) * 4, T)) return rc;
   if (int rc = dalloc(&E->d_perm_dyn, std::max<size_t>((size_t)E->n, 1) * 4, T)) return rc;
   if (int rc = dalloc(&E->d_romb, bytes.size(), T)) return rc;
-  if (int rc = dalloc(&E->d_dec_op, 512, T)) return rc;
   if (int rc = dalloc(&E->d_queue, 64, T)) return rc;
   CUDA_TRY(cudaMemcpy(E->d_romb, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(E->d_dec_op, dec_op.data(), 512, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaStreamCreateWithFlags(&E->cap_stream, cudaStreamNonBlocking));
   CUDA_TRY(cudaFuncSetAttribute(k_raster_preprocess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem()));
   const atari_config &c = E->cfg;
