@@ -94,6 +94,9 @@ def parse(argv=None):
                         "start state per cartridge, beside a run from the usual random start states and the oracle "
                         "on the host from the same shared start")
     p.add_argument("--window", type=int, default=10)
+    p.add_argument("--sweep", default=None,
+                   help="comma-separated env counts: frames/s and frames/s per env of the batched and plain forms "
+                        "and of the oracle at each count (paper Section 4, Fig. 2)")
     p.add_argument("--capture", action="store_true",
                    help="profiling run: W + K plain steps, no timing; prints each step's instructions retired and "
                         "TIA writes logged (the counts an ncu capture of one of these launches is divided by)")
@@ -610,6 +613,49 @@ def shape_dict(shape):
             "grouping": g & 3, "dispatch": 2 if g & 4 else 1}
 
 
+def sweep_run(args, config, counts, rank):
+    """Frames/s and frames/s per env against the number of envs (the paper's
+    Fig. 2 and its FPS-per-env discussion in Section 4): the batched form
+    (autotuned at each count), the plain form, and the oracle on the host
+    cores (a bounded sample at the larger counts), same cartridges and keys."""
+    import numpy as np
+    import torch
+
+    from paper_1907_08467_gb300 import synth
+    from paper_1907_08467_gb300.env import FORM_BATCHED, FORM_PLAIN
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    K, W = max(3, args.steps), max(3, args.warmup)
+    rows = []
+    cores = os.cpu_count() or 1
+    for n in counts:
+        w = synth.workload(config, n_envs=n)
+        acts = torch.from_numpy(synth.actions(700 + rank, K + W, n)).cuda()
+        row = {"n_envs": n}
+        for name, form in (("batched", FORM_BATCHED), ("plain", FORM_PLAIN)):
+            env = make_env(w, form, args, rank)
+            obs, rew, done = env.alloc_outputs()
+            ms, _, _ = timed_steps(lambda a: env.step(a, obs, rew, done), acts, K, W, flush, 1)
+            fps = n * w.frameskip * K / (sum(ms) / 1000.0)
+            row[name] = {"frames_per_s": fps, "frames_per_s_per_env": fps / n, "ms_per_step": sum(ms) / K}
+            if form == FORM_BATCHED:
+                row[name]["launch_shape"] = shape_dict(env.launch_shape())
+            env.close()
+        m = min(n, 256)
+        idx = np.linspace(0, n - 1, m).astype(np.int64)
+        o = _oracle_for(w, idx)
+        ha = acts.cpu().numpy()
+        t0, k = time.perf_counter(), 0
+        while k < K + W and (k < 3 or time.perf_counter() - t0 < 3.0):
+            o.step(ha[k][idx], n_threads=cores)
+            k += 1
+        ofps = m * w.frameskip * k / (time.perf_counter() - t0)
+        row["oracle"] = {"frames_per_s": ofps, "envs_timed": m, "cores": cores,
+                         "note": "rate of the timed sample; the oracle's rate does not grow with more envs than cores"}
+        rows.append(row)
+    return {"sweep": {"workload": synth.workload(config).name.split(",")[0], "config": config, "steps": K,
+                      "cpu_model": cpu_model(), "rows": rows, "l2": "flushed (256 MB write) before each step"}}
+
+
 def kernel_name(env, form):
     if form == "plain":
         return "k_interp_plain"
@@ -635,6 +681,11 @@ def main(argv=None):
     K, W = args.steps, args.warmup
     if args.divergence:
         res = divergence_run(args, w, rank)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
+    if args.sweep:
+        res = sweep_run(args, args.config, [int(x) for x in args.sweep.split(",")], rank)
         if rank == 0:
             print(json.dumps(res), flush=True)
         return
