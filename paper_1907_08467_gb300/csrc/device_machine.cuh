@@ -141,7 +141,10 @@ __device__ __forceinline__ uint32_t copy_bits(uint32_t nusiz) {
 __device__ __forceinline__ uint32_t player_bits(uint32_t grp, uint32_t refp) {
   return (refp & 8) ? (grp & 0xFF) : (__brev(grp & 0xFF) >> 24);
 }
-__device__ __forceinline__ M160 player_mask(uint32_t grp, uint32_t refp, uint32_t nusiz, uint32_t pos) {
+// Masks of the objects at pixel 0 (before the move to their position): the
+// widest (three copies, or a 32-pixel quad-size player) spans words 0..2, so
+// words 3 and 4 are always zero.
+__device__ __forceinline__ M160 player_base(uint32_t grp, uint32_t refp, uint32_t nusiz) {
   uint32_t g = player_bits(grp, refp);
   M160 m{0, 0, 0, 0, 0};
   uint32_t mode = nusiz & 7;
@@ -153,9 +156,9 @@ __device__ __forceinline__ M160 player_mask(uint32_t grp, uint32_t refp, uint32_
     m.w1 = (c & 4) ? g : 0u;
     m.w2 = (c & 8) ? g : 0u;
   }
-  return rot160(m, pos);
+  return m;
 }
-__device__ __forceinline__ M160 missile_mask(uint32_t nusiz, uint32_t pos) {
+__device__ __forceinline__ M160 missile_base(uint32_t nusiz) {
   uint32_t w = 1u << ((nusiz >> 4) & 3);
   uint32_t base = (1u << w) - 1u;
   M160 m{0, 0, 0, 0, 0};
@@ -163,12 +166,20 @@ __device__ __forceinline__ M160 missile_mask(uint32_t nusiz, uint32_t pos) {
   m.w0 = ((c & 1) ? base : 0u) | ((c & 2) ? (base << 16) : 0u);
   m.w1 = (c & 4) ? base : 0u;
   m.w2 = (c & 8) ? base : 0u;
-  return rot160(m, pos);
+  return m;
+}
+__device__ __forceinline__ M160 ball_base(uint32_t ctrlpf) {
+  uint32_t w = 1u << ((ctrlpf >> 4) & 3);
+  return M160{(1u << w) - 1u, 0, 0, 0, 0};
+}
+__device__ __forceinline__ M160 player_mask(uint32_t grp, uint32_t refp, uint32_t nusiz, uint32_t pos) {
+  return rot160(player_base(grp, refp, nusiz), pos);
+}
+__device__ __forceinline__ M160 missile_mask(uint32_t nusiz, uint32_t pos) {
+  return rot160(missile_base(nusiz), pos);
 }
 __device__ __forceinline__ M160 ball_mask(uint32_t ctrlpf, uint32_t pos) {
-  uint32_t w = 1u << ((ctrlpf >> 4) & 3);
-  M160 m{(1u << w) - 1u, 0, 0, 0, 0};
-  return rot160(m, pos);
+  return rot160(ball_base(ctrlpf), pos);
 }
 // 20 playfield bits of a half, bit b = 4-pixel block b from the left.
 __device__ __forceinline__ uint32_t pf20(uint32_t pf0, uint32_t pf1, uint32_t pf2) {
