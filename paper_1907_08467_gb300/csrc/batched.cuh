@@ -416,16 +416,15 @@ __device__ inline void render_rows_warp(RenderRegs &R, const uint32_t *recs, uin
       if (c >= end) break;
       R.prepare(k < 5 && cl + 68u + lane + 32u * k < c, lane);
       while (k < 5 && cl + 68u + lane + 32u * k < c) {
-        row[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
+        row[lane + 32 * k] = (uint8_t)R.pixel_k(k);
         ++k;
       }
       R.apply((rec >> 8) & 0x3F, rec & 0xFF, c);
       ++ri;
     }
     R.prepare(k < 5, lane);
-    if (__all_sync(0xFFFFFFFFu, k == 0)) R.row5(lane, line, row);
-    else
-      for (; k < 5; ++k) row[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
+    R.row_from(k, lane, row);
+    R.hmove_bar(lane, line, row);
   }
 }
 

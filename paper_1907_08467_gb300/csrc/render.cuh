@@ -24,10 +24,11 @@ struct RenderRegs {
   // Per lane, one nibble per column lane + 32k (bit 4k): v_* = the object
   // covers the column (players, missiles and ball with their enables,
   // playfield); sel = nibble k holds the colour class of the column after
-  // the priority rules.  Rebuilt for the objects in `dirty` before the next
-  // pixel is drawn.
-  uint32_t vp0, vp1, vm0, vm1, vbl, vpf, sel;
-  uint32_t dirty;  // 1 P0, 2 P1, 4 M0, 8 M1, 16 BL, 32 PF, 64 priority or score mode
+  // the priority rules; cw, c4 = the five pixel colours (bytes 0..3 of cw,
+  // byte 0 of c4), zero while blanked.  Rebuilt for what `dirty` names
+  // before the next pixel is drawn.
+  uint32_t vp0, vp1, vm0, vm1, vbl, vpf, sel, cw, c4;
+  uint32_t dirty;  // 1 P0, 2 P1, 4 M0, 8 M1, 16 BL, 32 PF, 64 priority or score mode, 128 colours or blanking
 
   // from a 64-byte snapshot (canonical bytes 0x20..0x5F)
   __device__ void load(const uint8_t *t) {
@@ -41,7 +42,7 @@ struct RenderRegs {
     uint64_t b = 0, l0 = 0;
     for (int i = 7; i >= 0; --i) { b = (b << 8) | t[40 + i]; l0 = (l0 << 8) | t[48 + i]; }
     bar = (b != NO_LINE && b >= l0 && b - l0 < 1024) ? (uint32_t)(b - l0) : ~0u;
-    dirty = 127;
+    dirty = 255;
   }
 
   static __device__ __forceinline__ uint32_t res_pos(uint32_t eff, uint32_t add, uint32_t hb) {
@@ -62,13 +63,13 @@ struct RenderRegs {
   // marked stale only when something its coverage is built from changes.
   __device__ void apply(uint32_t reg, uint32_t v, uint32_t eff) {
     switch (reg) {
-      case 0x01: vblank = v; break;
+      case 0x01: dirty |= (vblank ^ v) & 2 ? 128 : 0; vblank = v; break;
       case 0x04: dirty |= v != nusiz0 ? 1 | 4 : 0; nusiz0 = v; break;
       case 0x05: dirty |= v != nusiz1 ? 2 | 8 : 0; nusiz1 = v; break;
-      case 0x06: pal = (pal & 0xFFFF00FFu) | v << 8; break;
-      case 0x07: pal = (pal & 0xFF00FFFFu) | v << 16; break;
-      case 0x08: pal = (pal & 0x00FFFFFFu) | v << 24; break;
-      case 0x09: pal = (pal & 0xFFFFFF00u) | v; break;
+      case 0x06: pal = (pal & 0xFFFF00FFu) | v << 8; dirty |= 128; break;
+      case 0x07: pal = (pal & 0xFF00FFFFu) | v << 16; dirty |= 128; break;
+      case 0x08: pal = (pal & 0x00FFFFFFu) | v << 24; dirty |= 128; break;
+      case 0x09: pal = (pal & 0xFFFFFF00u) | v; dirty |= 128; break;
       case 0x0A:
         dirty |= ((ctrlpf ^ v) & 0x30 ? 16 : 0) | ((ctrlpf ^ v) & 1 ? 32 : 0) | ((ctrlpf ^ v) & 6 ? 64 : 0);
         ctrlpf = v; break;
@@ -143,6 +144,12 @@ struct RenderRegs {
     return (lo & 1u) | (lo >> 4 & 0x10u) | (lo >> 8 & 0x100u) | (lo >> 12 & 0x1000u) | ((uint32_t)(g >> 16) & 0x10000u);
   }
   __device__ __forceinline__ void refresh(uint32_t lane) {
+    if (dirty & 127) refresh_classes(lane);
+    cw = (vblank & 2) ? 0u : __byte_perm(pal, 0, sel) & 0xFEFEFEFEu;
+    c4 = (vblank & 2) ? 0u : __byte_perm(pal, 0, sel >> 16) & 0xFEu;
+    dirty = 0;
+  }
+  __device__ __forceinline__ void refresh_classes(uint32_t lane) {
     if (dirty & 1) {
       const uint32_t g = (vdelp0 & 1) ? grp0_old : grp0_new;
       vp0 = (g & 0xFF) ? cover(player_base(g, refp0, nusiz0), p0, lane) : 0u;
@@ -155,7 +162,6 @@ struct RenderRegs {
     if (dirty & 8) vm1 = ((enam1 & 2) && !(resmp1 & 2)) ? cover(missile_base(nusiz1), m1, lane) : 0u;
     if (dirty & 16) vbl = ((((vdelbl & 1) ? enabl_old : enabl_new) & 2)) ? cover(ball_base(ctrlpf), bl, lane) : 0u;
     if (dirty & 32) vpf = pf_cover(pf0, pf1, pf2, ctrlpf, lane);
-    dirty = 0;
     // Colour class of each column, all five at once on the nibble planes.
     // Normal priority: player 0 and missile 0, then player 1 and missile 1,
     // then playfield (in score mode coloured as player 0 left of column 80
@@ -185,26 +191,21 @@ struct RenderRegs {
   __device__ __forceinline__ void prepare(bool draws, uint32_t lane) {
     if (dirty != 0 && __any_sync(0xFFFFFFFFu, draws)) refresh(lane);
   }
-  // All five pixels of the lane on a line drawn from one register state
-  // (no write lands between them).
-  __device__ __forceinline__ void row5(uint32_t lane, uint32_t line, uint8_t *row) const {
-    if (vblank & 2) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) row[lane + 32 * k] = 0;
-      return;
-    }
-    const uint32_t c = __byte_perm(pal, 0, sel) & 0xFEFEFEFEu;  // columns k = 0..3
-    row[lane] = (line == bar && lane < 8) ? 0 : (uint8_t)c;
-    row[lane + 32] = (uint8_t)(c >> 8);
-    row[lane + 64] = (uint8_t)(c >> 16);
-    row[lane + 96] = (uint8_t)(c >> 24);
-    row[lane + 128] = (uint8_t)(__byte_perm(pal, 0, sel >> 16) & 0xFE);
+  // Pixels k0..4 of the lane on a line, drawn from one register state (no
+  // write lands between them); the stores before k0 are skipped.
+  __device__ __forceinline__ void row_from(uint32_t k0, uint32_t lane, uint8_t *row) const {
+    if (k0 == 0) row[lane] = (uint8_t)cw;
+    if (k0 <= 1) row[lane + 32] = (uint8_t)(cw >> 8);
+    if (k0 <= 2) row[lane + 64] = (uint8_t)(cw >> 16);
+    if (k0 <= 3) row[lane + 96] = (uint8_t)(cw >> 24);
+    if (k0 <= 4) row[lane + 128] = (uint8_t)c4;
   }
-  // Pixel of column lane + 32k on a frame-relative line (the lane's own column);
-  // prepare() has run since the last write.
-  __device__ __forceinline__ uint32_t pixel_k(uint32_t k, uint32_t lane, uint32_t line) const {
-    if ((vblank & 2) || (k == 0 && line == bar && lane < 8)) return 0;
-    return __byte_perm(pal, 0, sel >> (4 * k)) & 0xFE;
+  // Pixel of column lane + 32k (the lane's own column); prepare() has run
+  // since the last write.
+  __device__ __forceinline__ uint32_t pixel_k(uint32_t k) const { return __byte_perm(cw, c4, k); }
+  // The HMOVE bar blanks columns 0..7 of its line.
+  __device__ __forceinline__ void hmove_bar(uint32_t lane, uint32_t line, uint8_t *row) const {
+    if (line == bar && lane < 8) row[lane] = 0;
   }
 };
 
@@ -233,16 +234,15 @@ __device__ inline void render_frame_warp(RenderRegs &R, const uint32_t *recs, ui
         if (c >= end) break;
         R.prepare(k < 5 && cl + 68u + lane + 32u * k < c, lane);
         while (k < 5 && cl + 68u + lane + 32u * k < c) {
-          row_buf[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
+          row_buf[lane + 32 * k] = (uint8_t)R.pixel_k(k);
           ++k;
         }
         R.apply((rec >> 8) & 0x3F, rec & 0xFF, c);
         ++ri;
       }
       R.prepare(k < 5, lane);
-      if (__all_sync(0xFFFFFFFFu, k == 0)) R.row5(lane, line, row_buf);
-      else
-        for (; k < 5; ++k) row_buf[lane + 32 * k] = (uint8_t)R.pixel_k(k, lane, line);
+      R.row_from(k, lane, row_buf);
+      R.hmove_bar(lane, line, row_buf);
     }
     __syncwarp();
     const uint32_t *src = reinterpret_cast<const uint32_t *>(row_buf);
