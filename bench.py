@@ -50,8 +50,8 @@ SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 # never captured reports achieved = null.
 INTERP_CAPTURES = {
     # (kernel, envs per warp, opcode dispatch, config): (warp-inst per 6502 instruction, DRAM bytes per env-step)
-    ("k_interp_split", 32, 1, 3): (3070763231 / 600042217, (13062144 + 115156224) / 32768),
-    ("k_interp_split", 32, 1, 2): (443947155 / 94159103, (1270784 + 92672) / 4096),
+    ("k_interp_split", 32, 1, 3): (3059083490 / 600042217, (13269760 + 114794240) / 32768),
+    ("k_interp_split", 32, 1, 2): (444233555 / 94159103, (1267712 + 86016) / 4096),
 }
 # Algorithmic bytes of the fused rasterise + preprocess kernel per env-step,
 # besides 4 bytes per logged TIA write: snapshots and record counts of the two
@@ -61,9 +61,9 @@ INTERP_CAPTURES = {
 FUSED_FIXED_BYTES_PER_ENV_STEP = 2 * 64 + 2 * 8 + 3 * 7056 + 4 * 7056 + 7056 + 1
 # Warp instructions per env-step of the fused kernel (it is bound by issue,
 # not HBM), from the same captures: smsp__inst_executed.sum / env-steps.
-FUSED_WARP_INST_PER_ENV_STEP = {3: 9062309897 / 32768, 2: 1302428699 / 4096}
+FUSED_WARP_INST_PER_ENV_STEP = {3: 5979554498 / 32768, 2: 711969603 / 4096}
 # DRAM bytes per env-step of the fused kernel, from an ncu capture per config.
-FUSED_DRAM_BYTES_PER_ENV_STEP = {3: (865188352 + 1107893000) / 32768, 2: (109642240 + 95167232) / 4096}
+FUSED_DRAM_BYTES_PER_ENV_STEP = {3: (863958016 + 1106787000) / 32768, 2: (109476096 + 94397696) / 4096}
 
 
 def parse(argv=None):
