@@ -750,11 +750,16 @@ def main(argv=None):
             env.step_host(ha[s], ho, hr, hd)
         barrier(ws)
         t0 = time.perf_counter()
+        host_ms = []
         for s in range(K):
+            t1 = time.perf_counter()
             env.step_host(ha[3 + s], ho, hr, hd)
+            host_ms.append((time.perf_counter() - t1) * 1e3)
         dt = allreduce_max(time.perf_counter() - t0, ws)
+        hp50, hp99 = percentiles(host_ms)
         e2e = {"value": frames_all / dt, "unit": "frames/s", "h2d_bytes_per_step": int(ha[0].numel()),
-               "d2h_bytes_per_step": int(ho.numel() + hr.numel() * 4 + hd.numel())}
+               "d2h_bytes_per_step": int(ho.numel() + hr.numel() * 4 + hd.numel()),
+               "p50_step_ms": hp50, "p99_step_ms": hp99}
     roof = interp_roofline(prof, instr, kern, shape[0], shape_dict(shape)["dispatch"], args.config, w.n_envs,
                            w.frameskip)
     if roof and lane_rounds:

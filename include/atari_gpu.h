@@ -154,8 +154,12 @@ ATARI_API int atari_env_step(atari_env *env, const uint8_t *d_actions, uint8_t *
 /*
  * Same step with host buffers (the host round trip of Section 1's inference
  * path, for callers whose agent runs on the host): copies actions host->device, steps, and
- * copies obs / rewards / dones device->host on `stream`, then synchronises
- * the stream.  Host pointers may be pageable or pinned; NULL skips.
+ * copies obs / rewards / dones device->host, then returns with every copy
+ * complete.  Host pointers may be pageable or pinned (pinned lets the copies
+ * overlap the rendering); NULL skips.  In the batched form with stack output
+ * the env renders in chunks of envs on `stream` and copies each chunk's
+ * stacks back on a stream of its own while the next chunk renders; results
+ * are the same as atari_env_step's.  Other forms copy on `stream`.
  */
 ATARI_API int atari_env_step_host(atari_env *env, const uint8_t *actions, uint8_t *obs, int32_t *rewards,
                         uint8_t *dones, atari_stream stream);

@@ -492,6 +492,9 @@ int dalloc(T **p, size_t bytes, size_t &total) {
 }  // namespace
 
 // ------------------------------------------------------------------ env object
+// Chunks of envs in the overlapped host-buffer step (batched stack output).
+constexpr int HOST_CHUNKS = 8;
+
 struct atari_env {
   int device = 0;
   int n = 0, n_roms = 0;
@@ -532,6 +535,11 @@ struct atari_env {
   std::vector<int32_t> h_env_rom;
   std::vector<uint32_t> h_banks;
   cudaStream_t cap_stream = nullptr;
+  // atari_env_step_host, batched stack output: the stacks come back on two
+  // streams of their own, one chunk of envs at a time, while the next chunk
+  // renders
+  cudaStream_t copy_stream[2] = {};
+  cudaEvent_t copy_ev[HOST_CHUNKS + 1] = {};
   struct GraphEntry { const void *k[4]; cudaGraphExec_t exec; };
   std::vector<GraphEntry> graphs;
   // profiling: (slot, start, end) event triples of the launches since the last read
@@ -910,6 +918,10 @@ void atari_env_destroy(atari_env *E) {
                   E->d_perm_dyn};
   for (auto &g : E->graphs) cudaGraphExecDestroy(g.exec);
   if (E->cap_stream) cudaStreamDestroy(E->cap_stream);
+  for (auto cs : E->copy_stream)
+    if (cs) cudaStreamDestroy(cs);
+  for (auto e : E->copy_ev)
+    if (e) cudaEventDestroy(e);
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (auto &r : E->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -1005,7 +1017,7 @@ int launch_batched(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
   if (c.output_mode == ATARI_OUT_STACK) {
     ProfScope p(E, ATARI_PROF_FUSED, s);
     k_raster_preprocess<<<E->n, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma, E->d_ring,
-                                                                E->d_head, E->d_done, d_obs, E->n, c.log_cap, E->wpf, nullptr, nullptr);
+                                                                E->d_head, E->d_done, d_obs, E->n, c.log_cap, E->wpf, nullptr, nullptr, 0);
   } else if (d_obs) {
     ProfScope p(E, ATARI_PROF_RASTER, s);
     k_raster<<<(unsigned)((E->n + 3) / 4), 128, 0, s>>>(E->d_log, E->d_snap, E->d_meta, d_obs, (size_t)210 * 160,
@@ -1159,7 +1171,7 @@ int autotune(atari_env *E) {
         for (int rep = 0; rep < 2; ++rep) {
           cudaEventRecord(e0);
           k_raster_preprocess<<<E->n, 64 * wpf, fused_smem()>>>(E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma, E->d_ring,
-                                                               E->d_head, E->d_done, nullptr, E->n, E->cfg.log_cap, wpf, nullptr, nullptr);
+                                                               E->d_head, E->d_done, nullptr, E->n, E->cfg.log_cap, wpf, nullptr, nullptr, 0);
           cudaEventRecord(e1);
           cudaEventSynchronize(e1);
           cudaEventElapsedTime(&t, e0, e1);
@@ -1231,6 +1243,64 @@ int atari_env_step(atari_env *E, const uint8_t *d_actions, uint8_t *d_obs, int32
   return step_plain(E, d_actions, d_obs, d_rewards, d_dones, s);
 }
 
+namespace {
+// Host-buffer step of the batched form with stack output: the interpreter,
+// then the fused kernel in chunks of envs on the step stream; each chunk's
+// stacks are copied out while the next chunk renders, and rewards and dones
+// as soon as the interpreter is done.  Each chunk's copy is split in halves
+// over two copy streams: one device-to-host copy per stream moves about 40 %
+// of what two concurrent ones do.  Results are those of atari_env_step
+// (every env's fused work is independent of the others').
+int step_host_overlapped(atari_env *E, uint8_t *obs, int32_t *rewards, uint8_t *dones, cudaStream_t s) {
+  const atari_config &c = E->cfg;
+  const size_t ob = obs_bytes(c);
+  const int n = E->n;
+  if (!E->copy_stream[0]) {
+    for (auto &cs : E->copy_stream) CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (auto &e : E->copy_ev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaStream_t *cs = E->copy_stream;
+  BatchArgs a = batch_args(E, E->d_act, nullptr, nullptr);
+  if (E->grouping == 2) {
+    ProfScope p(E, ATARI_PROF_GROUP, s);
+    launch_regroup(E, s);
+  }
+  CUDA_TRY(cudaMemsetAsync(E->d_queue, 0, sizeof(int), s));
+  {
+    ProfScope p(E, ATARI_PROF_INTERP, s);
+    launch_interp(E, a, E->grid, s);
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaEventRecord(E->copy_ev[0], s));
+  CUDA_TRY(cudaStreamWaitEvent(cs[0], E->copy_ev[0], 0));
+  if (rewards) CUDA_TRY(cudaMemcpyAsync(rewards, E->d_rew, (size_t)n * 4, cudaMemcpyDeviceToHost, cs[0]));
+  if (dones) CUDA_TRY(cudaMemcpyAsync(dones, E->d_done, (size_t)n, cudaMemcpyDeviceToHost, cs[0]));
+  // chunks of at least 1024 envs (a few waves of the fused kernel each)
+  const int chunks = n >= 1024 * HOST_CHUNKS ? HOST_CHUNKS : n >= 4096 ? 4 : 1;
+  for (int k = 0; k < chunks; ++k) {
+    const int b0 = (int)((int64_t)n * k / chunks), b1 = (int)((int64_t)n * (k + 1) / chunks);
+    {
+      ProfScope p(E, ATARI_PROF_FUSED, s);
+      k_raster_preprocess<<<b1 - b0, 64 * E->wpf, fused_smem(), s>>>(
+          E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma, E->d_ring, E->d_head, E->d_done, E->d_obs_tmp, n,
+          c.log_cap, E->wpf, nullptr, nullptr, b0);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(E->copy_ev[k + 1], s));
+    const size_t lo = (size_t)b0 * ob, mid = (size_t)(b0 + (b1 - b0) / 2) * ob, hi = (size_t)b1 * ob;
+    for (int h = 0; h < 2; ++h) {
+      const size_t x0 = h ? mid : lo, x1 = h ? hi : mid;
+      CUDA_TRY(cudaStreamWaitEvent(cs[h], E->copy_ev[k + 1], 0));
+      if (x1 > x0) CUDA_TRY(cudaMemcpyAsync(obs + x0, E->d_obs_tmp + x0, x1 - x0, cudaMemcpyDeviceToHost, cs[h]));
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(cs[0]));
+  CUDA_TRY(cudaStreamSynchronize(cs[1]));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return 0;
+}
+}  // namespace
+
 int atari_env_step_host(atari_env *E, const uint8_t *actions, uint8_t *obs, int32_t *rewards, uint8_t *dones,
                         atari_stream stream) {
   g_err.clear();
@@ -1245,6 +1315,8 @@ int atari_env_step_host(atari_env *E, const uint8_t *actions, uint8_t *obs, int3
     E->bytes += dummy;
   }
   CUDA_TRY(cudaMemcpyAsync(E->d_act, actions, E->n, cudaMemcpyHostToDevice, s));
+  if (obs && E->cfg.form == ATARI_FORM_BATCHED && E->cfg.output_mode == ATARI_OUT_STACK)
+    return step_host_overlapped(E, obs, rewards, dones, s);
   if (int rc = atari_env_step(E, E->d_act, obs ? E->d_obs_tmp : nullptr, nullptr, nullptr, stream)) return rc;
   if (obs) CUDA_TRY(cudaMemcpyAsync(obs, E->d_obs_tmp, (size_t)E->n * ob, cudaMemcpyDeviceToHost, s));
   if (rewards) CUDA_TRY(cudaMemcpyAsync(rewards, E->d_rew, (size_t)E->n * 4, cudaMemcpyDeviceToHost, s));
@@ -1660,7 +1732,7 @@ int serve_tick(atari_env *E, const ServeTick &t, cudaStream_t s) {
   CUDA_TRY(cudaGetLastError());
   k_raster_preprocess<<<t.n_active, 64 * E->wpf, fused_smem(), s>>>(E->d_log, E->d_snap, E->d_bsnap, E->d_meta, E->d_luma,
                                                                    E->d_ring, E->d_head, E->d_done, t.d_obs,
-                                                                   t.n_active, c.log_cap, E->wpf, a.perm, a.opos);
+                                                                   t.n_active, c.log_cap, E->wpf, a.perm, a.opos, 0);
   CUDA_TRY(cudaGetLastError());
   return 0;
 }

@@ -435,16 +435,18 @@ __global__ void __launch_bounds__(256, 3) k_raster_preprocess(const uint32_t *lo
                                                            const uint8_t *luma_g, uint8_t *ring, uint8_t *head,
                                                            const uint8_t *done, uint8_t *obs, int n, int log_cap,
                                                            int warps_per_frame, const int32_t *perm,
-                                                           const int32_t *opos) {
+                                                           const int32_t *opos, int base) {
   extern __shared__ __align__(16) uint8_t sm[];
   uint8_t *fa = sm;                        // frame F-1, later the luma maximum
   uint8_t *fb = sm + FRAME_H * FRAME_W;    // frame F
   uint8_t *luma = fb + FRAME_H * FRAME_W;
   uint8_t *plane = luma + 128;
-  if ((int)blockIdx.x >= n) return;
-  // block b serves env slot perm[b] and writes its stack at position opos[b]
-  const int i = perm ? perm[blockIdx.x] : (int)blockIdx.x;
-  const int o = opos ? opos[blockIdx.x] : i;
+  // block b (counted from base) serves env slot perm[b] and writes its stack
+  // at position opos[b]
+  const int blk = base + (int)blockIdx.x;
+  if (blk >= n) return;
+  const int i = perm ? perm[blk] : blk;
+  const int o = opos ? opos[blk] : i;
   const int warp = threadIdx.x >> 5;
   for (int t = threadIdx.x; t < 128; t += blockDim.x) luma[t] = luma_g[t];
   if (warp < 2 * warps_per_frame) {

@@ -252,6 +252,32 @@ def test_host_step_matches_device_step():
         assert np.array_equal(da.cpu().numpy(), db)
 
 
+@pytest.mark.parametrize("n,pinned", [(100, False), (4099, True), (8195, True), (8195, False)])
+def test_host_step_batched_chunks_match_device_step(n, pinned):
+    """The batched form's host step renders in chunks of envs and copies each
+    chunk back while the next renders (8195 envs: eight ragged chunks, 4099:
+    four, 100 envs: one); stacks, rewards and dones equal the device step's, pinned or
+    pageable host buffers, and rewards / dones alone work too."""
+    w = synth.workload(2, n_envs=n)
+    a = AtariEnv.from_workload(w, form=FORM_BATCHED)
+    b = AtariEnv.from_workload(w, form=FORM_BATCHED)
+    acts = synth.actions(23, 6, n)
+    ho = torch.empty(b.obs_shape(), dtype=torch.uint8)
+    hr = torch.empty(n, dtype=torch.int32)
+    hd = torch.empty(n, dtype=torch.uint8)
+    if pinned:
+        ho, hr, hd = ho.pin_memory(), hr.pin_memory(), hd.pin_memory()
+    for s in range(6):
+        oa, ra, da = a.step(torch.from_numpy(acts[s]).cuda())
+        if s == 4:
+            b.step_host(acts[s], None, hr, hd)  # stacks not asked for: the plain host path
+            assert np.array_equal(ra.cpu().numpy(), hr.numpy()) and np.array_equal(da.cpu().numpy(), hd.numpy())
+            continue
+        b.step_host(acts[s], ho, hr, hd)
+        assert np.array_equal(oa.cpu().numpy(), ho.numpy())
+        assert np.array_equal(ra.cpu().numpy(), hr.numpy()) and np.array_equal(da.cpu().numpy(), hd.numpy())
+
+
 def test_batched_equals_plain_at_full_size():
     """Both forms on the 4096-env configuration for 15 steps: identical
     observations, rewards, dones and states (the autotuned launch shape
