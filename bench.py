@@ -77,6 +77,8 @@ def parse(argv=None):
     p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--serve-clients", type=int, default=64)
     p.add_argument("--n-envs", type=int, default=None)
+    p.add_argument("--idle-skip", type=int, default=1, choices=[0, 1],
+                   help="batched form: retire RIOT-timer wait-loop iterations at once (1) or run each (0)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
@@ -382,7 +384,7 @@ def make_env(w, form, args, rank):
     from paper_1907_08467_gb300 import synth
     from paper_1907_08467_gb300.env import AtariEnv
     kw = dict(envs_per_warp=args.envs_per_warp, envs_per_block=args.envs_per_block,
-              raster_warps_per_frame=args.warps_per_frame, tia_warps=args.tia_warps)
+              raster_warps_per_frame=args.warps_per_frame, tia_warps=args.tia_warps, idle_skip=args.idle_skip)
     if args.grouping:
         kw["grouping"] = args.grouping
     if args.dispatch:
@@ -811,6 +813,7 @@ def main(argv=None):
                        "output": "84x84x4 uint8 stack" if w.output_mode == 1 else "210x160 palette frame",
                        "form": args.form, "l2": "flushed (256 MB write) before each timed step",
                        "launch_shape": shape_dict(shape),
+                       "timer_wait_skip": bool(args.idle_skip) and args.form == "batched",
                        "parallelism": f"replicas x{ws}"},
             "plain": plain, "e2e": e2e, "roofline": roof, "roofline_fused": roof2, "kernels": kernels,
             "gpu_launches": gpu_launches, "m6502_inst_per_step": instr, "tia_log_records_per_step": logrec,

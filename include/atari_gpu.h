@@ -97,11 +97,15 @@ typedef struct {
     int dispatch;         /* batched form, the interpreter's hot opcode switch: 1 = every common opcode inline;
                              2 = compact (indirect forms, BIT, stack pushes and pulls, indexed and absolute
                              read-modify-writes through the general decoder: a smaller hot loop); 0 = autotune */
+    int idle_skip;        /* batched form: 1 = a RIOT-timer wait loop (LDA INTIM at PC, BNE back to PC) retires
+                             the iterations that read a nonzero timer value at once (cycles and instruction
+                             counts advanced exactly; same results), 0 = every iteration runs.  Default 1;
+                             the plain form runs every iteration */
 } atari_config;
 
 /* Fill *cfg with the paper's defaults: F = 4, no sticky actions, 30 cached
  * states, 64 start-up frames, up to 30 no-ops, stack output, plain form,
- * log_cap 4096, autotuned launch shapes, seed 1. */
+ * log_cap 4096, autotuned launch shapes, timer-wait skipping on, seed 1. */
 ATARI_API void atari_default_config(atari_config *cfg);
 
 /*
@@ -288,7 +292,9 @@ ATARI_API int atari_env_get_frames(atari_env *env, uint8_t *d_dst, atari_stream 
  * Device buffer owned by the caller, copied on `stream`. */
 ATARI_API int atari_env_get_cache(atari_env *env, void *d_dst, atari_stream stream);
 
-/* Counters of the last step: 6502 instructions retired (sum over envs), TIA
+/* Counters of the last step: 6502 instructions executed (sum over envs; the
+ * iterations of a RIOT-timer wait loop that the batched form retires at once,
+ * see idle_skip, are not counted), TIA
  * log records written, and lockstep issue rounds summed over the envs (each
  * env counts the rounds its warp issued, so instructions / lane_rounds is
  * the fraction of a warp's lanes that execute per round: the emulated-

@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(128) k_cache_run(uint8_t *work, uint8_t *snaps
   m.io = IoCtx{tia, iow};
   m.scheme = inf & 0xFF;
   m.wmask = 1u;
+  m.idle = 1u;
   m.load(st);
   m.set_log(nullptr, 0, nullptr);
   for (int f = 0; f < startup; ++f) {
@@ -573,9 +574,9 @@ int validate(const atari_config &c) {
   if (c.sticky != 0 && c.sticky != 1) return fail(ATARI_EINVAL, "sticky must be 0 or 1");
   if (c.envs_per_block < 0 || c.envs_per_block > 128 || c.envs_per_warp < 0 || c.envs_per_warp > 32 ||
       c.raster_warps_per_frame < 0 || c.raster_warps_per_frame > 4 || c.tia_warps < 0 || c.tia_warps > 3 ||
-      c.grouping < 0 || c.grouping > 2 || c.dispatch < 0 || c.dispatch > 2)
+      c.grouping < 0 || c.grouping > 2 || c.dispatch < 0 || c.dispatch > 2 || c.idle_skip < 0 || c.idle_skip > 1)
     return fail(ATARI_EINVAL, "envs_per_block must be 0..128, envs_per_warp 0..32, raster_warps_per_frame 0..4, "
-                              "tia_warps 0..3, grouping 0..2, dispatch 0..2");
+                              "tia_warps 0..3, grouping 0..2, dispatch 0..2, idle_skip 0..1");
   return 0;
 }
 
@@ -679,6 +680,7 @@ BatchArgs batch_args(atari_env *E, const uint8_t *d_actions, int32_t *d_rewards,
   a.first_slot = c.output_mode == ATARI_OUT_PALETTE ? 1 : 0;
   a.seed = c.seed;
   a.tia_off = c.tia_warps == 3 ? 1 : 0;
+  a.idle = c.idle_skip;
   return a;
 }
 
@@ -759,6 +761,7 @@ void atari_default_config(atari_config *c) {
   c->envs_per_block = 0;
   c->envs_per_warp = 0;
   c->raster_warps_per_frame = 0;
+  c->idle_skip = 1;
   c->seed = 1;
 }
 

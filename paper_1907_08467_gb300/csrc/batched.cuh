@@ -44,6 +44,7 @@ struct BatchArgs {
   int n_groups, lanes, E, rom_stage;  // rom_stage: bytes staged per block (largest cartridge)
   int frameskip, sticky, n_cache, log_cap, first_slot;
   int tia_off;               // split form test mode: the TIA side takes no events
+  int idle;                  // retire RIOT-timer wait-loop iterations at once
   uint64_t seed;
 };
 
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(128) k_interp_batched(BatchArgs a) {
         m.io = IoCtx{tia + TIA_STRIDE * j, iow + IO_STRIDE * j};
         m.scheme = inf & 0xFF;
         m.wmask = wmask;
+        m.idle = (uint32_t)a.idle;
         m.load(st);
         fast_step_env(m, st, i, o, a, (uint32_t)rom, (inf >> 8) & 0x7F, (inf >> 16) & 0x7F);
       }
@@ -308,6 +310,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_split(BatchArgs a) {
       m.q = q;
       m.scheme = inf & 0xFF;
       m.wmask = wmask;
+      m.idle = (uint32_t)a.idle;
       m.load(st);
     }
     __syncthreads();  // the envs' state is in shared memory before the TIA side starts

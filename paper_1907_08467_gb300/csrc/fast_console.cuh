@@ -468,6 +468,7 @@ struct FastConsoleT {
   uint32_t status, instret, frame_no;
   uint32_t rounds;         // lockstep issue rounds of this env's warp in the step (the same on every lane)
   uint32_t wmask;          // lanes of this warp running envs (lockstep issue)
+  uint32_t idle;           // retire RIOT-timer wait-loop iterations at once
   // split form: this env's TIA event queue and the CPU side's copies
   uint32_t *q;
   uint32_t qtail, qhead_seen, nreq, vsync_c, vblank_c, broken;  // qhead_seen: the TIA side's cursor as last read
@@ -775,17 +776,48 @@ struct FastConsoleT {
   __device__ __forceinline__ uint32_t inc(uint32_t v) { const uint32_t r = (v + 1) & 0xFF; fn = fz = r; return r; }
   __device__ __forceinline__ uint32_t dec(uint32_t v) { const uint32_t r = (v - 1) & 0xFF; fn = fz = r; return r; }
 
+  // ---- RIOT-timer wait loops ----
+  // LDA INTIM at pc with BNE back to pc right after it: an iteration that
+  // reads a nonzero timer value changes nothing but the cycle count (A and the
+  // N, Z flags are overwritten by the read that exits), and the read has no
+  // side effect.  With the timer counting in intervals of 2^sh >= 8 cycles, at
+  // least the loop's period (7 cycles, 8 when the branch crosses a page), the
+  // first read at or after the cycle where INTIM reaches 0 reads 0.  So the
+  // iterations before that read retire at once: the cycle count advances
+  // exactly as if they ran, and the returned cycle is where the exiting LDA
+  // starts.  They are not counted in instret, which counts the instructions
+  // the issue rounds execute.  Anything else (no such loop, a faster
+  // timer, the timer already at 0 or past it, a frame that would reach the
+  // line cap) returns k0 unchanged.
+  __device__ __forceinline__ uint32_t idle_forward(uint32_t w, uint32_t pc, uint32_t k0) {
+    const uint32_t a = (w >> 8) & 0xFFFF;
+    if ((a & 0x1285u) != 0x0284u || (w >> 24) != 0xD0u) return k0;  // INTIM (any mirror), then BNE
+    const uint32_t off = pc & 0xFFF;
+    if (off > 0xFFBu || rom8[bank * 4096u + off + 4] != 0xFBu) return k0;  // BNE offset -5: back to pc
+    const uint32_t sh = io.G(IO_TSH);
+    if (sh < 3) return k0;
+    const uint64_t l0 = SPLIT ? l0c : io.G64(IO_L0LO);
+    const uint64_t n0 = 76ull * l0 + k0 + 3 - (io.G64(IO_TCWLO) + 1);  // the read's cycle, as the timer counts it
+    const uint64_t zero = (uint64_t)io.G(IO_TV) << sh;                 // first cycle reading 0
+    if (n0 >= zero) return k0;
+    const uint32_t period = (((pc + 5) ^ pc) & 0xFF00) ? 8u : 7u;
+    const uint64_t it = (zero - n0 + period - 1) / period;
+    const uint64_t k1 = k0 + it * period;
+    if (k1 + 6 >= 76ull * CAP_LINES) return k0;
+    return (uint32_t)k1;
+  }
+
   // ---- one instruction, hot form ----
   // Returns false (with nothing changed) for the cases the general decoder
   // takes.  Each case sets the cycle count n and the next PC; the tail
   // applies the WSYNC stall.
   // w = cartridge bytes PC .. PC+3 of the current bank (fetch4).
   __device__ __forceinline__ bool exec(uint32_t w) {
-    const uint32_t k0 = kf;
     const uint32_t pc = PC;
     const uint32_t off = pc & 0xFFF;
     // no hot fetch may touch a hotspot: F8/F6 hotspots start at $FF6, F4's at $FF4
     if (!(pc & 0x1000) || off > (scheme == 3 ? 0xFF1u : scheme ? 0xFF3u : 0xFFCu)) return false;
+    const uint32_t k0 = kf;
     const uint32_t b1 = (w >> 8) & 0xFF;
     const uint32_t a16 = (w >> 8) & 0xFFFF;
     uint32_t n;
@@ -803,7 +835,8 @@ struct FastConsoleT {
   case OPI: { const uint32_t v = b1; BODY; n = 2; PC = pc + 2; break; }                                      \
   case OPZ: { const uint32_t v = rdz(b1, k0 + 2); BODY; n = 3; PC = pc + 2; break; }                          \
   case OPZX: { const uint32_t v = rdz(ZPX_, k0 + 3); BODY; n = 4; PC = pc + 2; break; }                       \
-  case OPA: { const uint32_t v = rd(a16, k0 + 3); BODY; n = 4; PC = pc + 3; break; }                          \
+  case OPA: { const uint32_t ka = (OPA == 0xAD && idle) ? idle_forward(w, pc, k0) : k0;                     \
+              const uint32_t v = rd(a16, ka + 3); BODY; n = 4 + (ka - k0); PC = pc + 3; break; }             \
   case OPAX: { const uint32_t ea = ABX_; n = 4 + XPG(a16, ea); const uint32_t v = rd(ea, k0 + n - 1); BODY;   \
                PC = pc + 3; break; }                                                                          \
   case OPAY: { const uint32_t ea = ABY_; n = 4 + XPG(a16, ea); const uint32_t v = rd(ea, k0 + n - 1); BODY;   \

@@ -28,7 +28,8 @@ class _Config(C.Structure):
                 ("startup_frames", C.c_int), ("max_noops", C.c_int), ("output_mode", C.c_int),
                 ("form", C.c_int), ("log_cap", C.c_int), ("envs_per_block", C.c_int),
                 ("envs_per_warp", C.c_int), ("raster_warps_per_frame", C.c_int), ("seed", C.c_uint64),
-                ("tia_warps", C.c_int), ("grouping", C.c_int), ("dispatch", C.c_int)]
+                ("tia_warps", C.c_int), ("grouping", C.c_int), ("dispatch", C.c_int),
+                ("idle_skip", C.c_int)]
 
 
 class _Meta(C.Structure):
@@ -111,10 +112,10 @@ def _check(rc: int):
 
 def make_config(frameskip=4, sticky=False, n_cache=30, startup_frames=64, max_noops=30,
                 output_mode=OUT_STACK, form=FORM_PLAIN, log_cap=4096, envs_per_block=0, envs_per_warp=0,
-                raster_warps_per_frame=0, seed=1, tia_warps=0, grouping=0, dispatch=0) -> _Config:
+                raster_warps_per_frame=0, seed=1, tia_warps=0, grouping=0, dispatch=0, idle_skip=1) -> _Config:
     return _Config(frameskip, int(sticky), n_cache, startup_frames, max_noops, output_mode, form,
                    log_cap, envs_per_block, envs_per_warp, raster_warps_per_frame, seed, tia_warps, grouping,
-                   dispatch)
+                   dispatch, int(idle_skip))
 
 
 def footprint(n_envs: int, n_roms: int, **cfg) -> int:
@@ -253,8 +254,9 @@ class AtariEnv:
         return out
 
     def counters(self, stream=None):
-        """(6502 instructions retired, TIA writes logged, lockstep issue rounds
-        summed over envs) of the last step."""
+        """(6502 instructions executed, TIA writes logged, lockstep issue rounds
+        summed over envs) of the last step; timer-wait iterations retired at
+        once are not counted as executed."""
         a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
         _check(self.lib.atari_env_counters(self.h, C.byref(a), C.byref(b), C.byref(c), _stream(stream)))
         return a.value, b.value, c.value

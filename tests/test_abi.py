@@ -39,6 +39,7 @@ def test_default_config_and_footprint(lib):
     c = E._Config()
     lib.atari_default_config(C.byref(c))
     assert (c.frameskip, c.n_cache, c.startup_frames, c.max_noops, c.log_cap) == (4, 30, 64, 30, 4096)
+    assert c.idle_skip == 1 and E.make_config().idle_skip == 1
     f1 = lib.atari_env_footprint(1000, 8, C.byref(c))
     f2 = lib.atari_env_footprint(2000, 8, C.byref(c))
     assert f2 > f1 > 0
@@ -68,7 +69,8 @@ def test_rejects_bad_rom_size_before_touching_the_device(lib):
 
 def test_rejects_bad_config(lib):
     rom = b"\xea" * 4096
-    for field, val in (("frameskip", 1), ("n_cache", 0), ("output_mode", 7), ("log_cap", 10), ("form", 9)):
+    for field, val in (("frameskip", 1), ("n_cache", 0), ("output_mode", 7), ("log_cap", 10), ("form", 9),
+                       ("idle_skip", 2)):
         c = E.make_config()
         setattr(c, field, val)
         rc, _ = _create(lib, [rom], [4096], cfg=c)
