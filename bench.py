@@ -43,15 +43,17 @@ SM_COUNT, SMSP_PER_SM, SM_MAX_MHZ = 152, 4, 2070.0
 # bytes per env-step, from one ncu capture per (kernel, envs per warp,
 # workload config): smsp__inst_executed.sum and dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch, divided by the 6502 instructions that
-# launch retired (counted by the kernel itself) and by its env-steps.  The
-# bench multiplies the ratio by the instructions retired in the profiled
+# launch executed (counted by the kernel itself) and by its env-steps.  The
+# bench multiplies the ratio by the instructions executed in the profiled
 # launches, counted live, and divides by their live CUDA-event duration.
 # A shape captured on another workload is used with its source named; a shape
 # never captured reports achieved = null.
 INTERP_CAPTURES = {
-    # (kernel, envs per warp, opcode dispatch, config): (warp-inst per 6502 instruction, DRAM bytes per env-step)
-    ("k_interp_split", 32, 1, 3): (3059083490 / 600042217, (13269760 + 114794240) / 32768),
-    ("k_interp_split", 32, 1, 2): (444233555 / 94159103, (1267712 + 86016) / 4096),
+    # (kernel, envs per warp, opcode dispatch, config): (warp-inst per executed 6502 instruction, DRAM bytes per env-step)
+    ("k_interp_split", 32, 1, 3): (2234457806 / 433965025, (13179648 + 114831104) / 32768),
+    ("k_interp_split", 32, 2, 3): (2213124575 / 433965025, (13961216 + 124522240) / 32768),
+    ("k_interp_split", 32, 1, 2): (445471194 / 94159103, (1266688 + 88064) / 4096),
+    ("k_interp_split", 32, 2, 2): (442946243 / 94159103, (1260288 + 104192) / 4096),
 }
 # Algorithmic bytes of the fused rasterise + preprocess kernel per env-step,
 # besides 4 bytes per logged TIA write: snapshots and record counts of the two
